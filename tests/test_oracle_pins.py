@@ -1,0 +1,406 @@
+"""Pins of the CPU oracle against things other than itself.
+
+Every test here checks an oracle function against a closed form, an invariant,
+an independent library routine, a hand-derived worked example under
+tests/golden/, or brute force on a tiny input, so that a dropped term, a wrong
+sign or index, or a transposed operand in the oracle fails at least one test.
+"""
+import json
+import os
+
+import numpy as np
+import pytest
+import torch
+import torch.nn.functional as F
+
+import oracle as O
+from paper_2508_07071_gb300 import synth
+
+
+def coord_image(h, w, c=3):
+    """Pixel value is a known closed form of its coordinates."""
+    y, x, ch = np.meshgrid(np.arange(h), np.arange(w), np.arange(c), indexing="ij")
+    return ((7 * y + 3 * x + 11 * ch) % 256).astype(np.uint8)
+
+
+# ---------------------------------------------------------------- crop / swap / split
+
+
+def test_crop_closed_form():
+    img = coord_image(9, 13)
+    out = O.crop(img, 5, 2, 4, 3)
+    assert out.shape == (3, 4, 3)
+    for j in range(3):
+        for i in range(4):
+            for c in range(3):
+                assert out[j, i, c] == (7 * (2 + j) + 3 * (5 + i) + 11 * c) % 256
+
+
+@pytest.mark.parametrize("roi", [(-1, 0, 2, 2), (0, 0, 14, 1), (12, 8, 2, 2), (0, 0, 0, 3)])
+def test_crop_rejects_outside(roi):
+    with pytest.raises(ValueError):
+        O.crop(coord_image(9, 13), *roi)
+
+
+def test_swap_is_involution_and_reverses():
+    img = synth.packed_image(3, 7, 5)
+    assert np.array_equal(O.swap_rb(O.swap_rb(img)), img)
+    s = O.swap_rb(img)
+    assert np.array_equal(s[..., 0], img[..., 2]) and np.array_equal(s[..., 2], img[..., 0])
+    assert np.array_equal(s[..., 1], img[..., 1])
+
+
+def test_split_closed_form():
+    img = coord_image(4, 6)
+    planes = O.split(img)
+    assert planes.shape == (3, 4, 6)
+    for c in range(3):
+        for y in range(4):
+            for x in range(6):
+                assert planes[c, y, x] == (7 * y + 3 * x + 11 * c) % 256
+
+
+# ---------------------------------------------------------------- bilinear resize
+
+
+def test_resize_golden_rows(golden_dir):
+    spec = json.load(open(os.path.join(golden_dir, "resize_halfpixel_rows.json")))
+    for case in spec["cases"]:
+        src = np.array(case["src"], dtype=np.float64).reshape(1, -1, 1)
+        out = O.resize_bilinear(src, case["dst_w"], 1)
+        np.testing.assert_allclose(out[0, :, 0], case["expected"], rtol=0, atol=1e-12)
+
+
+def test_resize_identity_is_copy():
+    img = O.to_float(synth.packed_image(4, 23, 31))
+    assert np.array_equal(O.resize_bilinear(img, 31, 23), img)
+
+
+def test_resize_one_pixel_source_is_constant():
+    img = np.full((1, 1, 3), 0.0)
+    img[0, 0] = (17.0, 99.0, 250.0)
+    out = O.resize_bilinear(img, 9, 5)
+    assert np.array_equal(out, np.broadcast_to(img, (5, 9, 3)))
+
+
+def test_resize_exact_2x_is_block_mean():
+    img = O.to_float(synth.packed_image(5, 18, 26))
+    out = O.resize_bilinear(img, 13, 9)
+    blocks = img.reshape(9, 2, 13, 2, 3).mean(axis=(1, 3))
+    np.testing.assert_allclose(out, blocks, rtol=0, atol=1e-12)
+
+
+def test_resize_exact_4x_uses_middle_pair():
+    # scale 4: u = 4d + 1.5, so every output is the mean of source pixels 4d+1, 4d+2
+    img = O.to_float(synth.packed_image(6, 16, 24))
+    out = O.resize_bilinear(img, 6, 4)
+    sub = img[1::4][:, :] + img[2::4][:, :]
+    sub = (sub[:, 1::4] + sub[:, 2::4]) / 4.0
+    np.testing.assert_allclose(out, sub, rtol=0, atol=1e-12)
+
+
+def test_resize_reproduces_linear_ramp():
+    # S(x, y) = x + 2y; bilinear interpolation is exact on affine functions,
+    # so D(d, e) = u(d) + 2 v(e) wherever the sample needs no clamping.
+    h, w = 30, 40
+    ys, xs = np.meshgrid(np.arange(h), np.arange(w), indexing="ij")
+    img = (xs + 2 * ys).astype(np.float64)[..., None]
+    out_w, out_h = 17, 23
+    out = O.resize_bilinear(img, out_w, out_h)[..., 0]
+    u = (np.arange(out_w) + 0.5) * w / out_w - 0.5
+    v = (np.arange(out_h) + 0.5) * h / out_h - 0.5
+    ok_u = (u >= 0) & (u <= w - 1)
+    ok_v = (v >= 0) & (v <= h - 1)
+    expect = u[None, :] + 2 * v[:, None]
+    mask = ok_v[:, None] & ok_u[None, :]
+    assert mask.sum() > 0.8 * mask.size
+    np.testing.assert_allclose(out[mask], expect[mask], rtol=0, atol=1e-9)
+
+
+@pytest.mark.parametrize("src_hw,dst_hw", [((30, 40), (17, 23)), ((7, 5), (19, 13)),
+                                           ((480, 640), (224, 224)), ((64, 33), (64, 128)),
+                                           ((3, 2), (3, 2)), ((1, 9), (4, 4))])
+def test_resize_matches_torch_interpolate(src_hw, dst_hw):
+    # torch's bilinear with align_corners=False uses the same half-pixel
+    # mapping and border clamp; an independent library routine.
+    img = O.to_float(synth.packed_image(7, *src_hw))
+    ours = O.resize_bilinear(img, dst_hw[1], dst_hw[0])
+    t = torch.from_numpy(np.ascontiguousarray(img.transpose(2, 0, 1)))[None]
+    ref = F.interpolate(t, size=dst_hw, mode="bilinear", align_corners=False)[0]
+    np.testing.assert_allclose(ours, ref.numpy().transpose(1, 2, 0), rtol=0, atol=1e-9)
+
+
+def test_resize_is_separable_brute_force():
+    # brute force on a tiny image: four explicit taps per output pixel
+    img = O.to_float(synth.packed_image(8, 5, 4))
+    out = O.resize_bilinear(img, 7, 3)
+    for e in range(3):
+        v = min(max((e + 0.5) * 5 / 3 - 0.5, 0.0), 4.0)
+        y0 = int(np.floor(v)); y1 = min(y0 + 1, 4); b = v - y0
+        for d in range(7):
+            u = min(max((d + 0.5) * 4 / 7 - 0.5, 0.0), 3.0)
+            x0 = int(np.floor(u)); x1 = min(x0 + 1, 3); a = u - x0
+            want = ((1 - a) * (1 - b) * img[y0, x0] + a * (1 - b) * img[y0, x1]
+                    + (1 - a) * b * img[y1, x0] + a * b * img[y1, x1])
+            np.testing.assert_allclose(out[e, d], want, rtol=0, atol=1e-12)
+
+
+# ---------------------------------------------------------------- NV12 / BT.601
+
+
+def nv12_from_planes(luma, u, v):
+    h, w = luma.shape
+    uv = np.empty((h // 2, w), dtype=np.uint8)
+    uv[:, 0::2] = u
+    uv[:, 1::2] = v
+    return np.concatenate([luma, uv], axis=0)
+
+
+def test_bt601_coefficients_closed_form():
+    c_y, c_rv, c_gu, c_gv, c_bu = O.bt601_limited_coefficients()
+    np.testing.assert_allclose([c_y, c_rv, c_gu, c_gv, c_bu],
+                               [1.164383562, 1.596026786, 0.391762290, 0.812967647, 2.017232143],
+                               atol=1e-8)
+
+
+def test_nv12_black_white_gray():
+    for yv, want in [(16, 0.0), (235, 255.0), (126, 110 * 255 / 219)]:
+        f = nv12_from_planes(np.full((4, 6), yv, np.uint8), np.full((2, 3), 128, np.uint8),
+                             np.full((2, 3), 128, np.uint8))
+        np.testing.assert_allclose(O.nv12_to_rgb(f), want, atol=1e-9)
+
+
+def test_nv12_inverts_bt601_forward_transform():
+    # Decode integer NV12 frames with the oracle, then re-encode the RGB with
+    # the forward BT.601 definition, E'Y = Kr R + Kg G + Kb B,
+    # E'Cb = (B - E'Y) / (2 (1 - Kb)), E'Cr = (R - E'Y) / (2 (1 - Kr)),
+    # Y = 16 + 219 E'Y, Cb = 128 + 224 E'Cb, Cr = 128 + 224 E'Cr (E' = RGB/255):
+    # every pixel that needed no clamping must give back its Y, U, V.
+    frame = synth.nv12_frames(12, 1, 32, 48, lo=60, hi=190)[0]
+    rgb = O.nv12_to_rgb(frame)
+    kr, kb = 0.299, 0.114
+    kg = 1 - kr - kb
+    e = rgb / 255.0
+    ey = kr * e[..., 0] + kg * e[..., 1] + kb * e[..., 2]
+    Y = 16 + 219 * ey
+    U = 128 + 224 * (e[..., 2] - ey) / (2 * (1 - kb))
+    V = 128 + 224 * (e[..., 0] - ey) / (2 * (1 - kr))
+    luma = frame[:32].astype(np.float64)
+    u = np.repeat(np.repeat(frame[32:, 0::2], 2, axis=0), 2, axis=1).astype(np.float64)
+    v = np.repeat(np.repeat(frame[32:, 1::2], 2, axis=0), 2, axis=1).astype(np.float64)
+    inside = np.all((rgb > 0) & (rgb < 255), axis=-1)
+    assert inside.sum() > 100
+    np.testing.assert_allclose(Y[inside], luma[inside], atol=1e-9)
+    np.testing.assert_allclose(U[inside], u[inside], atol=1e-9)
+    np.testing.assert_allclose(V[inside], v[inside], atol=1e-9)
+
+
+def test_nv12_decode_matches_per_pixel_brute_force():
+    frame = synth.nv12_frames(9, 1, 6, 8)[0]
+    out = O.nv12_to_rgb(frame)
+    c_y, c_rv, c_gu, c_gv, c_bu = O.bt601_limited_coefficients()
+    for y in range(6):
+        for x in range(8):
+            Y = float(frame[y, x])
+            U = float(frame[6 + y // 2, 2 * (x // 2)])
+            V = float(frame[6 + y // 2, 2 * (x // 2) + 1])
+            r = c_y * (Y - 16) + c_rv * (V - 128)
+            g = c_y * (Y - 16) - c_gu * (U - 128) - c_gv * (V - 128)
+            b = c_y * (Y - 16) + c_bu * (U - 128)
+            want = np.clip([r, g, b], 0, 255)
+            np.testing.assert_allclose(out[y, x], want, atol=1e-12)
+
+
+def test_nv12_clamps():
+    f = nv12_from_planes(np.full((2, 2), 255, np.uint8), np.full((1, 1), 255, np.uint8),
+                         np.full((1, 1), 255, np.uint8))
+    rgb = O.nv12_to_rgb(f)
+    assert rgb.max() == 255.0 and rgb.min() >= 0.0
+    assert rgb[0, 0, 0] == 255.0 and rgb[0, 0, 2] == 255.0
+
+
+# ---------------------------------------------------------------- letterbox
+
+
+def test_letterbox_1280x720_to_640():
+    assert O.letterbox_geometry(1280, 720, 640, 640) == (640, 360, 0, 140)
+    rng = np.random.default_rng(1)
+    img = rng.uniform(0, 255, size=(720, 1280, 3))
+    out = O.letterbox(img, 640, 640, 114.0)
+    assert np.all(out[:140] == 114.0) and np.all(out[500:] == 114.0)
+    blocks = img.reshape(360, 2, 640, 2, 3).mean(axis=(1, 3))
+    np.testing.assert_allclose(out[140:500], blocks, rtol=0, atol=1e-10)
+
+
+def test_letterbox_odd_padding_floor_on_top():
+    # 100x51 into 64x64: r = 0.64, height round(32.64) = 33, 31 pad rows: 15 top, 16 bottom
+    assert O.letterbox_geometry(100, 51, 64, 64) == (64, 33, 0, 15)
+    out = O.letterbox(np.zeros((51, 100, 3)), 64, 64, 7.0)
+    assert np.all(out[:15] == 7.0) and np.all(out[48:] == 7.0) and np.all(out[15:48] == 0.0)
+    # portrait source pads left/right
+    assert O.letterbox_geometry(30, 60, 64, 64) == (32, 64, 16, 0)
+
+
+# ---------------------------------------------------------------- compute ops
+
+
+def test_normalise_constant_image_closed_form():
+    mean = (0.485, 0.456, 0.406)
+    std = (0.229, 0.224, 0.225)
+    src = np.empty((4, 4, 3), np.uint8)
+    src[..., 0], src[..., 1], src[..., 2] = 10, 20, 30      # B, G, R
+    out = O.preprocess_packed(src, (0, 0, 4, 4), 2, 2, swap=True,
+                              mul=1 / 255, sub=mean, div=std)
+    # after BGR->RGB the first plane is R=30 and uses mean[0], std[0]
+    for c, val in enumerate((30, 20, 10)):
+        np.testing.assert_allclose(out[c], (val / 255 - mean[c]) / std[c], atol=1e-12)
+    np.testing.assert_allclose(out[0, 0, 0], (30 / 255 - 0.485) / 0.229, atol=1e-12)
+    np.testing.assert_allclose(out[0, 0, 0], -1.60416130, atol=1e-8)
+
+
+def test_imagenet_extremes():
+    mean = np.array((0.485, 0.456, 0.406)); std = np.array((0.229, 0.224, 0.225))
+    lo = O.divide(O.subtract(O.multiply(np.zeros((1, 1, 3)), 1 / 255), mean), std)[0, 0]
+    hi = O.divide(O.subtract(O.multiply(np.full((1, 1, 3), 255.0), 1 / 255), mean), std)[0, 0]
+    np.testing.assert_allclose(lo, [-2.117904, -2.035714, -1.804444], atol=1e-6)
+    np.testing.assert_allclose(hi, [2.248908, 2.428571, 2.640000], atol=1e-6)
+
+
+def test_add_saturate_u8():
+    x = np.array([[[0, 5, 250]]], np.uint8)
+    assert O.add_saturate_u8(x, 10).tolist() == [[[10, 15, 255]]]
+    assert O.add_saturate_u8(x, -10).tolist() == [[[0, 0, 240]]]
+    assert O.add_saturate_u8(x, (1, -6, 5)).tolist() == [[[1, 0, 255]]]
+
+
+def test_saturate_cast_u8():
+    x = np.array([2.5, 3.5, -0.6, 255.5, 254.5, 300.0, 0.49, 127.5])
+    assert O.saturate_cast_u8(x).tolist() == [2, 4, 0, 255, 254, 255, 0, 128]
+
+
+# ---------------------------------------------------------------- output casts
+
+
+def _random_f32(n, seed, lo_exp=-20, hi_exp=8):
+    rng = np.random.default_rng(seed)
+    mant = rng.uniform(1, 2, n)
+    exp = rng.integers(lo_exp, hi_exp, n)
+    sign = rng.choice([-1.0, 1.0], n)
+    return (sign * np.ldexp(mant, exp)).astype(np.float32)
+
+
+def test_bf16_matches_torch():
+    x = _random_f32(200000, 1, -100, 100)
+    ref = torch.from_numpy(x).to(torch.bfloat16).to(torch.float64).numpy()
+    assert np.array_equal(O.round_bf16(x.astype(np.float64)), ref)
+
+
+def test_f16_matches_numpy_half():
+    x = np.concatenate([_random_f32(200000, 2, -24, 15).astype(np.float64),
+                        np.random.default_rng(3).uniform(-60000, 60000, 10000)])
+    ref = x.astype(np.float16).astype(np.float64)
+    assert np.array_equal(O.round_f16(x), ref)
+
+
+def test_e4m3_matches_torch_float8():
+    x = np.concatenate([_random_f32(200000, 4, -12, 9),
+                        np.random.default_rng(5).uniform(-448, 448, 20000).astype(np.float32)])
+    x = x[np.abs(x) <= 448]
+    ref = torch.from_numpy(x).to(torch.float8_e4m3fn).to(torch.float64).numpy()
+    assert np.array_equal(O.round_e4m3(x.astype(np.float64)), ref)
+
+
+def test_e4m3_golden_ties_and_saturation(golden_dir):
+    spec = json.load(open(os.path.join(golden_dir, "e4m3_ties.json")))
+    for case in spec["cases"]:
+        assert O.round_e4m3(np.array([case["q"]]))[0] == case["expected"], case
+
+
+def test_e4m3_decode_all_codes_round_trip():
+    codes = np.arange(256, dtype=np.uint8)
+    vals = O.decode_e4m3(codes)
+    finite = ~np.isnan(vals)
+    assert finite.sum() == 254                      # 0x7F and 0xFF are NaN
+    assert np.nanmax(vals) == 448.0 and np.nanmin(vals) == -448.0
+    # every finite code is a fixed point of the rounding
+    assert np.array_equal(O.round_e4m3(vals[finite]), vals[finite])
+    ref = torch.from_numpy(codes.copy()).view(torch.float8_e4m3fn).to(torch.float64).numpy()
+    assert np.array_equal(vals[finite], ref[finite])
+
+
+def test_decode_bf16():
+    x = _random_f32(1000, 6)
+    bits = torch.from_numpy(x).to(torch.bfloat16).view(torch.int16).numpy().view(np.uint16)
+    ref = torch.from_numpy(x).to(torch.bfloat16).to(torch.float64).numpy()
+    assert np.array_equal(O.decode_bf16(bits), ref)
+
+
+def test_format_ulp():
+    assert O.format_ulp(np.array([1.0]), "bf16")[0] == 2.0 ** -7
+    assert O.format_ulp(np.array([1.5]), "f16")[0] == 2.0 ** -10
+    assert O.format_ulp(np.array([300.0]), "e4m3")[0] == 32.0
+    assert O.format_ulp(np.array([1e-9]), "e4m3")[0] == 2.0 ** -9
+
+
+def test_quantize_e4m3_scale():
+    v = np.array([0.0, 0.5, 1.0, 1.1])
+    q = O.quantize_e4m3(v, 1.0 / 448.0)
+    assert q.tolist() == [0.0, 224.0, 448.0, 448.0]
+
+
+# ---------------------------------------------------------------- vertical chain
+
+
+def test_vertical_chain_no_contraction():
+    # x*c0 = 1 + 2^-11 + 2^-24 is a tie at binary32 and rounds to 1 + 2^-11;
+    # adding -1 then gives exactly 2^-11. A fused multiply-add would keep the
+    # 2^-24 and return 2^-11 + 2^-24.
+    x = np.array([1 + 2.0 ** -12], np.float32)
+    out = O.vertical_chain_f32(x, [O.KIND_MUL, O.KIND_ADD], [1 + 2.0 ** -12, -1.0])
+    assert out[0] == np.float32(2.0 ** -11)
+
+
+def test_vertical_chain_order():
+    x = np.array([2.0], np.float32)
+    assert O.vertical_chain_f32(x, [O.KIND_MUL, O.KIND_ADD], [3.0, 1.0])[0] == 7.0
+    assert O.vertical_chain_f32(x, [O.KIND_ADD, O.KIND_MUL], [1.0, 3.0])[0] == 9.0
+
+
+def test_vertical_chain_identity_and_error_bound():
+    x = synth.f32_uniform(2, 4096)
+    kinds = [O.KIND_MUL, O.KIND_ADD] * 50
+    assert np.array_equal(O.vertical_chain_f32(x, kinds, [1.0, 0.0] * 50), x)
+    k, c = synth.chain_constants(2, 1000)
+    assert k[0] == O.KIND_MUL and k[1] == O.KIND_ADD
+    got = O.vertical_chain_f32(x, k, c).astype(np.float64)
+    exact = x.astype(np.float64)
+    for kind, cc in zip(k, c.astype(np.float64)):
+        exact = exact * cc if kind == O.KIND_MUL else exact + cc
+    # each of the 1000 ops adds at most half an ulp of a value of magnitude < 2
+    assert np.max(np.abs(got - exact)) < 1000 * 2.0 ** -23
+
+
+# ---------------------------------------------------------------- whole chains
+
+
+def test_preprocess_chain_is_op_by_op():
+    src = synth.packed_image(11, 40, 50)
+    roi = (3, 4, 30, 20)
+    out = O.preprocess_packed(src, roi, 16, 12, swap=True, mul=2.0, sub=(1, 2, 3), div=(4, 5, 6))
+    t = src[4:24, 3:33].astype(np.float64)
+    t = F.interpolate(torch.from_numpy(np.ascontiguousarray(t.transpose(2, 0, 1)))[None],
+                      size=(12, 16), mode="bilinear", align_corners=False)[0].numpy()
+    t = t[::-1]                                            # BGR -> RGB on planes
+    want = (t * 2.0 - np.array([1, 2, 3.0])[:, None, None]) / np.array([4, 5, 6.0])[:, None, None]
+    np.testing.assert_allclose(out, want, atol=1e-10)
+
+
+def test_integer_chain_bit_exact_brute_force():
+    src = coord_image(9, 13)
+    out = O.integer_chain_packed(src, (2, 1, 5, 4), swap=True, add_k=(100, -50, 0))
+    for j in range(4):
+        for i in range(5):
+            for c in range(3):
+                val = (7 * (1 + j) + 3 * (2 + i) + 11 * (2 - c)) % 256
+                val = min(255, max(0, val + (100, -50, 0)[c]))
+                assert out[j, i, c] == val
