@@ -1,0 +1,445 @@
+"""Benchmark of the fused preprocessing path on GB300.
+
+Default workload (N=1): 256 NV12 1280x720 frames -> BT.601 RGB -> letterbox
+640x640 (pad 114) -> x1/255 -> planar BF16, one fused launch per step.
+value = algorithmic bytes / device time (GB/s), beside the unfused
+one-kernel-per-op chain on the same GPU, the HBM roofline of the fused kernel
+and the CPU oracle timed on the host cores.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--workload nv12|single|hf|vchain]
+  python bench.py --impl reference ...   # the CPU oracle on a bounded sample
+
+Under torchrun every rank runs its own batch (weak scaling, no collective on
+the data path); rank 0 prints one JSON line.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "Fused GB/s vs 8 TB/s HBM & speedup over unfused per-op kernels, same GB300"
+
+
+def measured_peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        d = json.load(open(path))
+        return float(d["hbm_gbs"]), "measured"
+    return 6800.0, "fallback"
+
+
+# ------------------------------------------------------------------ workloads
+
+
+class Workload:
+    """Inputs resident in HBM plus the fused and unfused calls of one step."""
+
+    name = ""
+    unit = "GB/s"
+
+    def step(self, stream):  # fused: one pass of the hot path
+        raise NotImplementedError
+
+    def step_unfused(self, stream):
+        raise NotImplementedError
+
+
+class NV12Letterbox(Workload):
+    def __init__(self, F, W, synth, metrics, torch, n, fmt="bf16", seed=3):
+        cfg = W.NV12
+        self.F, self.torch = F, torch
+        self.n, self.h, self.w, self.out = n, cfg["h"], cfg["w"], cfg["out"]
+        self.fmt = fmt
+        code = {"bf16": F.FKL_BF16, "f16": F.FKL_F16, "e4m3": F.FKL_E4M3, "f32": F.FKL_F32}[fmt]
+        tdt = {"bf16": torch.bfloat16, "f16": torch.float16, "e4m3": torch.float8_e4m3fn,
+               "f32": torch.float32}[fmt]
+        self.el = {"bf16": 2, "f16": 2, "e4m3": 1, "f32": 4}[fmt]
+        self.frames_host = synth.nv12_frames(seed, n, self.h, self.w)
+        self.frames = torch.from_numpy(self.frames_host).cuda()
+        self.dst = torch.empty((n, 3, self.out, self.out), dtype=tdt, device="cuda")
+        self.pipe = F.Pipeline(W.nv12_letterbox_chain(code, out=self.out, pad=cfg["pad"]))
+        self.ins = [F.as_fkl(self.frames[i], F.FKL_LAYOUT_NV12) for i in range(n)]
+        self.o = F.as_fkl(self.dst, F.FKL_LAYOUT_NCHW)
+        dw, dh = metrics.letterbox_size(self.w, self.h, self.out, self.out)
+        self.bytes = n * (metrics.nv12_tap_bytes(0, 0, self.w, self.h, dw, dh)
+                          + metrics.out_bytes(1, self.out, self.out, self.el))
+        self.name = (f"NV12 {n}x{self.w}x{self.h} -> BT.601 -> letterbox {self.out}x{self.out} pad 114 "
+                     f"-> x1/255 -> planar {fmt}")
+        self.launches_per_step = (n + 255) // 256
+        self.ws = None
+        self.h2d_bytes = self.frames_host.nbytes
+        self.d2h_bytes = self.dst.numel() * self.el
+
+    def step(self, stream):
+        self.F.fkl_execute_batch(self.pipe.handle, self.ins, None, self.o, stream=stream)
+
+    def step_unfused(self, stream):
+        if self.ws is None:
+            nb = self.F.fkl_unfused_workspace_bytes(self.pipe.handle, self.ins, None, self.o)
+            self.ws = self.torch.empty(nb, dtype=self.torch.uint8, device="cuda")
+            self.ws_bytes = nb
+        self.F.fkl_execute_batch_unfused(self.pipe.handle, self.ins, None, self.o,
+                                         self.ws.data_ptr(), self.ws_bytes, stream=stream)
+
+    def unfused_bytes(self):
+        # decode (read NV12, write f32 RGB), letterbox (read taps, write f32),
+        # x1/255 (read + write f32), split+cast (read f32, write out)
+        rgb = self.h * self.w * 12
+        img = self.out * self.out * 12
+        nv12 = self.h * self.w * 3 // 2
+        per = (nv12 + rgb) + (rgb + img) + (2 * img) + (img + self.out * self.out * 3 * self.el)
+        return self.n * per
+
+    def e2e_setup(self):
+        torch = self.torch
+        self.host_in = torch.from_numpy(self.frames_host).pin_memory()
+        self.host_out = torch.empty(self.dst.shape, dtype=self.dst.dtype).pin_memory()
+
+    def e2e_step(self, stream):
+        self.frames.copy_(self.host_in, non_blocking=True)
+        self.step(stream)
+        self.host_out.copy_(self.dst, non_blocking=True)
+
+    def oracle_sample(self, O, k):
+        O.preprocess_nv12(self.frames_host[k % self.n], self.out, self.out, pad=114.0, mul=1 / 255)
+        return self.bytes / self.n
+
+
+class PackedBatch(Workload):
+    """Crops of packed u8 frames -> resize -> BGR->RGB -> normalise -> planar."""
+
+    def __init__(self, F, W, synth, metrics, torch, single: bool):
+        self.F, self.torch = F, torch
+        if single:
+            cfg = W.SINGLE
+            src = synth.packed_image(0, cfg["src_h"], cfg["src_w"])
+            rois = np.array([cfg["roi"]], np.int32)
+            n, ow, oh = 1, cfg["out_w"], cfg["out_h"]
+            self.name = "1920x1080 u8 BGR, crop 640x480@(320,200) -> 224x224 -> RGB -> /255 -> norm -> planar f32"
+        else:
+            cfg = W.HF
+            src = synth.packed_image(1, cfg["src_h"], cfg["src_w"])
+            rois = synth.crop_rois(1, cfg["n"], cfg["src_w"], cfg["src_h"], cfg["w_range"], cfg["h_range"])
+            n, ow, oh = cfg["n"], cfg["out_w"], cfg["out_h"]
+            self.name = "50 crops of 3840x2160 u8 -> 128x64 -> RGB -> /255 -> norm -> planar f32 [50,3,64,128]"
+        self.n, self.rois, self.src_host = n, rois, src
+        self.src = torch.from_numpy(src).cuda()
+        self.dst = torch.empty((n, 3, oh, ow), dtype=torch.float32, device="cuda")
+        self.pipe = F.Pipeline(W.normalize_chain(ow, oh))
+        self.ins = [F.as_fkl(self.src)] * n
+        self.o = F.as_fkl(self.dst, F.FKL_LAYOUT_NCHW)
+        self.bytes = sum(metrics.packed_tap_bytes(r[2], r[3], ow, oh) for r in rois) + \
+            metrics.out_bytes(n, oh, ow, 4)
+        self.ow, self.oh = ow, oh
+        self.launches_per_step = 1
+        self.ws = None
+        self.h2d_bytes = src.nbytes
+        self.d2h_bytes = self.dst.numel() * 4
+        # L2 is larger than this working set: flush between timed steps
+        self.flush = torch.empty(256 * 1024 * 1024, dtype=torch.uint8, device="cuda")
+
+    def step(self, stream):
+        self.F.fkl_execute_batch(self.pipe.handle, self.ins, self.rois, self.o, stream=stream)
+
+    def step_unfused(self, stream):
+        if self.ws is None:
+            nb = self.F.fkl_unfused_workspace_bytes(self.pipe.handle, self.ins, self.rois, self.o)
+            self.ws = self.torch.empty(nb, dtype=self.torch.uint8, device="cuda")
+            self.ws_bytes = nb
+        self.F.fkl_execute_batch_unfused(self.pipe.handle, self.ins, self.rois, self.o,
+                                         self.ws.data_ptr(), self.ws_bytes, stream=stream)
+
+    def between_steps(self):
+        self.flush.fill_(1)
+
+    def unfused_bytes(self):
+        # resize writes a float32 image; swap, x1/255, -mean, /std each read
+        # and write one; split reads one and writes the float32 planes
+        img = self.oh * self.ow * 12
+        taps = self.bytes - self.n * img
+        return taps + self.n * 11 * img
+
+    def e2e_setup(self):
+        self.host_in = self.torch.from_numpy(self.src_host).pin_memory()
+        self.host_out = self.torch.empty(self.dst.shape, dtype=self.dst.dtype).pin_memory()
+
+    def e2e_step(self, stream):
+        self.src.copy_(self.host_in, non_blocking=True)
+        self.step(stream)
+        self.host_out.copy_(self.dst, non_blocking=True)
+
+    def oracle_sample(self, O, k):
+        import paper_2508_07071_gb300.workloads as W
+        r = self.rois[k % self.n]
+        O.preprocess_packed(self.src_host, r, self.ow, self.oh, swap=True, mul=1 / 255,
+                            sub=W.IMAGENET_MEAN, div=W.IMAGENET_STD)
+        return self.bytes / self.n
+
+
+class VChain(Workload):
+    def __init__(self, F, W, synth, metrics, torch, L):
+        self.F, self.torch = F, torch
+        n = W.VCHAIN["n"]
+        self.n, self.L = n, L
+        self.x_host = synth.f32_uniform(2, n)
+        self.x = torch.from_numpy(self.x_host).cuda()
+        self.y = torch.empty_like(self.x)
+        kinds, consts = synth.chain_constants(2, L)
+        self.kinds, self.consts = kinds, consts
+        self.pipe = F.Pipeline(W.vertical_chain(kinds, consts))
+        self.i, self.o = F.as_fkl(self.x), F.as_fkl(self.y)
+        self.bytes = 8 * n
+        self.name = f"64M f32 uniform[-1,1], {L} alternating mul/add (FMA off), f32 out"
+        self.launches_per_step = max(1, (L + 4095) // 4096)
+        self.h2d_bytes = 4 * n
+        self.d2h_bytes = 4 * n
+
+    def step(self, stream):
+        self.F.fkl_execute(self.pipe.handle, self.i, self.o, stream=stream)
+
+    def step_unfused(self, stream):
+        self.F.fkl_execute_batch_unfused(self.pipe.handle, [self.i], None, self.o, 0, 0, stream=stream)
+
+    def unfused_bytes(self):
+        return 8 * self.n * max(1, self.L)
+
+    def e2e_setup(self):
+        self.host_in = self.torch.from_numpy(self.x_host).pin_memory()
+        self.host_out = self.torch.empty_like(self.host_in).pin_memory()
+
+    def e2e_step(self, stream):
+        self.x.copy_(self.host_in, non_blocking=True)
+        self.step(stream)
+        self.host_out.copy_(self.y, non_blocking=True)
+
+    def oracle_sample(self, O, k):
+        m = 1 << 20
+        O.vertical_chain_f32(self.x_host[(k * m) % self.n:][:m], self.kinds, self.consts)
+        return 8 * m
+
+
+def make_workload(args, F, W, synth, metrics, torch):
+    if args.workload == "nv12":
+        return NV12Letterbox(F, W, synth, metrics, torch, args.frames, args.out_dtype)
+    if args.workload in ("single", "hf"):
+        return PackedBatch(F, W, synth, metrics, torch, single=args.workload == "single")
+    if args.workload == "vchain":
+        return VChain(F, W, synth, metrics, torch, args.chain_len)
+    raise SystemExit(f"unknown workload {args.workload}")
+
+
+# ------------------------------------------------------------------ timing
+
+
+def time_steps(torch, fn, K, stream, between=None):
+    """Device time of K calls, each bracketed by events on `stream`; an
+    optional `between` (L2 flush) runs outside the bracketed regions."""
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(K)]
+    for a, b in ev:
+        if between:
+            between()
+        a.record(stream)
+        fn(stream)
+        b.record(stream)
+    torch.cuda.synchronize()
+    return [a.elapsed_time(b) for a, b in ev]
+
+
+def run_ours(args):
+    import torch
+    import torch.distributed as dist
+
+    rank, world = int(os.environ.get("RANK", "0")), int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    if world > 1:
+        dist.init_process_group("nccl")
+
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_2508_07071_gb300 import fkl as F, metrics, synth, workloads as W
+
+    wl = make_workload(args, F, W, synth, metrics, torch)
+    stream = torch.cuda.Stream()
+    between = getattr(wl, "between_steps", None)
+    with torch.cuda.stream(stream):
+        for _ in range(args.warmup):
+            wl.step(stream)
+        torch.cuda.synchronize()
+        if world > 1:
+            dist.barrier()
+        sampler = metrics.ClockSampler(local)
+        sampler.start()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        times = time_steps(torch, wl.step, args.steps, stream, between)
+        wall = time.perf_counter() - t0
+        sampler.stop()
+        if world > 1:
+            dist.barrier()
+        dev_ms = float(np.sum(times))
+        if world > 1:
+            t = torch.tensor([dev_ms], device="cuda")
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            dev_ms = float(t.item())
+        ms_per_step = dev_ms / args.steps
+        kernel_ms = float(np.mean(times)) / wl.launches_per_step
+
+        # unfused chain on the same GPU (a few steps)
+        ku = min(args.steps, args.unfused_steps)
+        unfused_ms = None
+        if ku > 0:
+            wl.step_unfused(stream)
+            torch.cuda.synchronize()
+            unfused_ms = float(np.mean(time_steps(torch, wl.step_unfused, ku, stream, between)))
+
+        # end to end through the public call with host buffers
+        ke = min(args.steps, args.e2e_steps)
+        e2e_ms = None
+        if ke > 0:
+            wl.e2e_setup()
+            for _ in range(2):
+                wl.e2e_step(stream)
+            torch.cuda.synchronize()
+            e2e_ms = float(np.mean(time_steps(torch, wl.e2e_step, ke, stream)))
+
+    peak, peak_kind = measured_peaks()
+    total_bytes = wl.bytes * world
+    value = total_bytes / (ms_per_step * 1e-3) / 1e9
+    achieved = wl.bytes / wl.launches_per_step / (kernel_ms * 1e-3) / 1e9
+    line = {
+        "metric": METRIC,
+        "value": round(value, 1),
+        "unit": "GB/s",
+        "n_gpus": world,
+        "steps": args.steps,
+        "warmup": args.warmup,
+        "ms_per_step": round(ms_per_step, 5),
+        "higher_is_better": True,
+        "scaling": "weak",
+        "vs_baseline": None,
+        "dtype": "f32",
+        "data": "synthetic (seeded), resident in HBM",
+        "config": {"workload": wl.name, "algorithmic_bytes_per_step": int(wl.bytes),
+                   "l2": getattr(wl, "l2_note", "inputs+outputs larger than L2 (no flush)" if between is None
+                                 else "L2 flushed (256 MiB write) between timed steps, outside the events"),
+                   "parallelism": f"replicas x{world}", "launch_shape": list(F.fkl_pipeline_get_shape(wl.pipe.handle))
+                   if hasattr(wl, "pipe") else None,
+                   "kernel": F.fkl_pipeline_kernel_name(wl.pipe.handle)},
+        "unfused": None if unfused_ms is None else {
+            "ms_per_step": round(unfused_ms, 4), "speedup": round(unfused_ms / ms_per_step, 2),
+            "traffic_ratio": round(wl.unfused_bytes() / wl.bytes, 2), "steps": ku,
+            "launches_per_step": getattr(wl, "unfused_launches", None)},
+        "roofline": {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
+                     "frac": round(achieved / peak, 4), "traffic": None,
+                     "peak_source": f"{peak_kind} copy bandwidth (MEASURED_PEAKS.json hbm_gbs)"
+                     if peak_kind == "measured" else "fallback 6.8 TB/s",
+                     "frac_of_8tbs": round(achieved / 8000.0, 4)},
+        "e2e": None if e2e_ms is None else {
+            "value": round(wl.bytes * world / (e2e_ms * 1e-3) / 1e9, 1), "unit": "GB/s",
+            "ms_per_step": round(e2e_ms, 4), "h2d_bytes_per_step": int(wl.h2d_bytes),
+            "d2h_bytes_per_step": int(wl.d2h_bytes), "steps": ke},
+        "gpu_launches": int(args.steps * wl.launches_per_step),
+        "clocks": sampler.summary(),
+        "wall_s_timed": round(wall, 4),
+    }
+    if rank == 0 and not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline(wl, args)
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
+
+
+def cpu_baseline(wl, args, budget_s=None):
+    import oracle as O
+    budget = budget_s if budget_s is not None else args.cpu_seconds
+    t0 = time.perf_counter()
+    b = wl.oracle_sample(O, 0)
+    one = time.perf_counter() - t0
+    k = int(max(1, min(64, budget / max(one, 1e-6))))
+    t0 = time.perf_counter()
+    nbytes = 0
+    for i in range(k):
+        nbytes += wl.oracle_sample(O, i)
+    dt = time.perf_counter() - t0
+    return {"value": round(nbytes / dt / 1e9, 6), "unit": "GB/s", "cores": 1, "kind": "oracle",
+            "sample": f"{k} unit(s) of the workload (images/frames, or 1M-element slices), "
+                      f"{dt:.1f} s, float64 numpy, single thread"}
+
+
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    import oracle as O
+    import torch
+    from paper_2508_07071_gb300 import synth, workloads as W, metrics
+
+    class _F:  # the reference arm touches no GPU: only the synthetic inputs
+        pass
+
+    cfg = W.NV12
+    if args.workload == "nv12":
+        frames = synth.nv12_frames(3, 4, cfg["h"], cfg["w"])
+        dw, dh = metrics.letterbox_size(cfg["w"], cfg["h"], cfg["out"], cfg["out"])
+        el = {"bf16": 2, "f16": 2, "e4m3": 1, "f32": 4}[args.out_dtype]
+        per = metrics.nv12_tap_bytes(0, 0, cfg["w"], cfg["h"], dw, dh) + metrics.out_bytes(1, 640, 640, el)
+
+        def one(k):
+            O.preprocess_nv12(frames[k % 4], 640, 640, pad=114.0, mul=1 / 255)
+            return per
+        name = f"NV12 1280x720 -> letterbox 640 -> planar {args.out_dtype} (one frame per step)"
+    else:
+        raise SystemExit("--impl reference supports --workload nv12")
+    for k in range(args.warmup):
+        one(k)
+    t0 = time.perf_counter()
+    nbytes = sum(one(k) for k in range(args.steps))
+    dt = time.perf_counter() - t0
+    val = nbytes / dt / 1e9
+    print(json.dumps({
+        "impl": "reference", "metric": METRIC, "value": round(val, 6), "unit": "GB/s", "n_gpus": 1,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(dt / args.steps * 1e3, 3),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic (seeded)", "config": {"workload": name},
+        "cpu_baseline": {"value": round(val, 6), "unit": "GB/s", "cores": 1, "kind": "oracle",
+                         "sample": "one 1280x720 frame per step, float64 numpy, single thread"},
+        "e2e": {"value": round(val, 6), "unit": "GB/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=200)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="nv12", choices=["nv12", "single", "hf", "vchain"])
+    ap.add_argument("--out-dtype", default="bf16", choices=["bf16", "f16", "e4m3", "f32"])
+    ap.add_argument("--frames", type=int, default=256)
+    ap.add_argument("--chain-len", type=int, default=10)
+    ap.add_argument("--unfused-steps", type=int, default=5)
+    ap.add_argument("--e2e-steps", type=int, default=10)
+    ap.add_argument("--cpu-seconds", type=float, default=10.0)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        raise SystemExit("--warmup must be >= 3")
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

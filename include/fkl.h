@@ -1,0 +1,246 @@
+/*
+ * fkl.h -- C ABI of the fused image-preprocessing library for GB300 (sm_103a).
+ *
+ * The library follows the Fused Kernel method (paper §IV): a user chain is one
+ * Read Operation (ROp), any number of Compute Operations (COps) and one Write
+ * Operation (WOp), run as ONE CUDA kernel whose intermediates stay in
+ * registers (vertical fusion, paper §II and Fig. 3), over one image or a batch
+ * of independent images in one launch (horizontal fusion, paper §II Fig. 5 and
+ * §IV-B BatchRead/BatchWrite). Functions return descriptions of work and
+ * launch nothing until an execute call (the lazy final interface of §IV-D).
+ *
+ * Memory: every tensor is caller-owned device memory (borrowed for the length
+ * of the call and of the work it enqueues). The library allocates no
+ * intermediate images (paper §VI-L). Streams are the caller's; all execute
+ * calls are asynchronous on the given stream (NULL = legacy default stream).
+ * No call synchronises the device except where stated.
+ *
+ * Errors: every call returns an fkl_status; on failure a thread-local message
+ * is available from fkl_last_error(). Invalid arguments are rejected before
+ * anything is enqueued. There is no CPU fallback: a chain that no compiled
+ * kernel implements is FKL_ERR_UNSUPPORTED.
+ *
+ * Thread safety: distinct pipelines may be used from distinct threads; one
+ * pipeline may be executed concurrently (it holds no per-call state).
+ */
+#ifndef FKL_H_
+#define FKL_H_
+
+#include <stddef.h>
+#include <stdint.h>
+
+#if defined(__GNUC__)
+#define FKL_API __attribute__((visibility("default")))
+#else
+#define FKL_API
+#endif
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ------------------------------------------------------------------------ */
+/* Status codes                                                             */
+/* ------------------------------------------------------------------------ */
+typedef enum {
+  FKL_OK = 0,
+  FKL_ERR_INVALID = 1,     /* bad argument: grammar, dims, dtype, pitch, ROI */
+  FKL_ERR_UNSUPPORTED = 2, /* valid chain with no compiled kernel           */
+  FKL_ERR_OOM = 3,         /* host allocation failed                        */
+  FKL_ERR_CUDA = 4,        /* a CUDA runtime call failed (message has it)   */
+  FKL_ERR_TIMEOUT = 5      /* a bounded device wait gave up                 */
+} fkl_status;
+
+/* ------------------------------------------------------------------------ */
+/* Tensors                                                                  */
+/* ------------------------------------------------------------------------ */
+enum {                 /* element types                                     */
+  FKL_U8 = 0,
+  FKL_F32 = 1,
+  FKL_F16 = 2,         /* IEEE binary16                                     */
+  FKL_BF16 = 3,
+  FKL_E4M3 = 4         /* OCP FP8 E4M3 (finite-only, max 448)               */
+};
+
+enum {                 /* layouts and the meaning of dims[]                 */
+  FKL_LAYOUT_LINEAR = 0, /* dims = {N}: N contiguous elements               */
+  FKL_LAYOUT_HWC = 1,    /* dims = {H, W, C}: packed pixels, rows pitch_bytes apart */
+  FKL_LAYOUT_NV12 = 2,   /* dims = {H, W}: u8 luma rows, then H/2 rows of
+                            interleaved (U, V) pairs starting at
+                            data + H * pitch_bytes, same pitch; H, W even   */
+  FKL_LAYOUT_NCHW = 3,   /* dims = {N, C, H, W}: planar; rows pitch_bytes
+                            apart, planes H * pitch_bytes apart              */
+  FKL_LAYOUT_NHWC = 4    /* dims = {N, H, W, C}: packed; rows pitch_bytes
+                            apart, images H * pitch_bytes apart              */
+};
+
+typedef struct {
+  void* data;            /* device pointer, caller-owned                      */
+  int64_t dims[4];       /* see the layout; unused entries 0                  */
+  int64_t pitch_bytes;   /* bytes between rows; 0 = tightly packed rows       */
+  int32_t dtype;         /* FKL_U8 ...                                        */
+  int32_t layout;        /* FKL_LAYOUT_...                                    */
+} fkl_tensor;
+
+/* ------------------------------------------------------------------------ */
+/* Operation descriptors (the IOps of paper §IV-A/§IV-B)                     */
+/* ------------------------------------------------------------------------ */
+enum {
+  /* Read Operations (paper Table I "ReadType"): the first descriptor.      */
+  FKL_OP_READ_U8C3 = 1,  /* packed 3-channel u8 image (HWC)                 */
+  FKL_OP_READ_NV12 = 2,  /* NV12 frame, decoded BT.601 limited range to RGB */
+  FKL_OP_READ_F32 = 3,   /* linear float32 tensor                           */
+
+  /* Read modifiers: together with the source they form the one ROp.       */
+  FKL_OP_CROP = 10,      /* i[0..3] = x, y, w, h of the window read        */
+  FKL_OP_RESIZE = 11,    /* i[0], i[1] = output width, height; bilinear,
+                            half-pixel centres, border clamp               */
+  FKL_OP_LETTERBOX = 12, /* i[0], i[1] = output width, height; f[0] = pad
+                            value in source units; aspect-preserving fit,
+                            size floor(s*r + 0.5), centred, odd pad pixel
+                            at the bottom/right                            */
+
+  /* Compute Operations (paper Table I "UnaryType"/"BinaryType").          */
+  FKL_OP_SWAP_RB = 20,   /* BGR <-> RGB: reverse the 3 channels             */
+  FKL_OP_MUL = 21,       /* x * f[c]   (3-channel chains: f[0..2]; F32: f[0]) */
+  FKL_OP_ADD = 22,       /* x + f[c]                                        */
+  FKL_OP_SUB = 23,       /* x - f[c]                                        */
+  FKL_OP_DIV = 24,       /* x / f[c], IEEE division                         */
+  FKL_OP_ADD_SAT_U8 = 25,/* u8 chains: clamp(x + i[c], 0, 255)              */
+
+  /* Write Operations (paper Table I "WriteType"): the last descriptor.    */
+  FKL_OP_WRITE_PACKED = 40, /* i[0] = output dtype; packed (HWC / linear)   */
+  FKL_OP_WRITE_SPLIT = 41   /* i[0] = output dtype; planar (paper Fig. 9
+                               Split); for FKL_E4M3, f[0] = per-tensor
+                               scale s > 0 and the stored code is
+                               satfinite_rne(x / s)                         */
+};
+
+typedef struct {
+  int32_t op;            /* FKL_OP_...                                      */
+  float f[8];            /* float parameters                                */
+  int32_t i[8];          /* integer parameters                              */
+} fkl_op_desc;
+
+typedef struct fkl_pipeline_s* fkl_pipeline;  /* library-owned handle        */
+
+/* ------------------------------------------------------------------------ */
+/* Pipelines                                                                */
+/* ------------------------------------------------------------------------ */
+
+/*
+ * Bind a chain (paper §IV-C TransformDPP: ROp -> COp* -> WOp, §IV-D executor)
+ * to one compiled kernel.
+ *
+ * ops[0] is a READ_*; then optional read modifiers (CROP, then RESIZE or
+ * LETTERBOX); then COps; ops[n_ops-1] is a WRITE_*. Anything else is
+ * FKL_ERR_INVALID. The kernel is chosen from a fixed set compiled ahead of
+ * time from C++17 templates (one instantiation per chain shape):
+ *   READ_U8C3 [CROP] RESIZE [SWAP_RB] [MUL] [ADD|SUB] [DIV] WRITE_{SPLIT,PACKED}
+ *        (float math; output F32/F16/BF16/E4M3)
+ *   READ_NV12 (RESIZE|LETTERBOX) [SWAP_RB] [MUL] [ADD|SUB] [DIV] WRITE_{SPLIT,PACKED}
+ *   READ_U8C3 [CROP] [SWAP_RB] [ADD_SAT_U8] WRITE_{SPLIT,PACKED} (U8 output)
+ *   READ_F32 (MUL|ADD){0..65536} WRITE_PACKED(F32)   (vertical chain)
+ * An absent MUL/ADD/SUB/DIV is bound as its identity (x*1, x-0, x/1 are
+ * exact, so the result equals the shorter chain bit for bit). A chain of the
+ * right grammar outside this set returns FKL_ERR_UNSUPPORTED.
+ *
+ * On success *out owns host memory only; free it with fkl_pipeline_destroy.
+ */
+FKL_API fkl_status fkl_pipeline_create(const fkl_op_desc* ops, int32_t n_ops,
+                               fkl_pipeline* out);
+
+/*
+ * Run the chain once: one image `in` to one output `out` (batch of one).
+ * Image chains: `in` is HWC u8 (READ_U8C3) or NV12 (READ_NV12); the ROI is the
+ * CROP descriptor's, else the whole image. `out` is NCHW (WRITE_SPLIT) or
+ * NHWC (WRITE_PACKED) with N = 1 and the dtype the WOp names; its H, W must
+ * equal the RESIZE/LETTERBOX size (the ROI size when there is no resize).
+ * Vertical chains: `in` and `out` are LINEAR F32 of the same length (may
+ * alias). stream is a cudaStream_t. One kernel launch per call (vertical
+ * chains longer than 4096 ops use one launch per 4096 ops).
+ */
+FKL_API fkl_status fkl_execute(fkl_pipeline p, const fkl_tensor* in, fkl_tensor* out,
+                       void* stream);
+
+/*
+ * Horizontal fusion (paper §IV-B BatchRead/BatchWrite): n independent images
+ * ins[0..n-1] (each its own size and pointer; the same pointer may repeat,
+ * e.g. many crops of one frame) into out[n, C, H, W] (or [n, H, W, C]).
+ * rois: n x 4 int32 (x, y, w, h) on the host, or NULL to use the CROP
+ * descriptor (or the whole image) for every image. Every ROI must lie inside
+ * its image. One launch covers up to 256 images; larger n uses ceil(n/256)
+ * launches.
+ */
+FKL_API fkl_status fkl_execute_batch(fkl_pipeline p, int32_t n, const fkl_tensor* ins,
+                             const int32_t* rois, fkl_tensor* out,
+                             void* stream);
+
+/* Release a pipeline. NULL is ignored. */
+FKL_API void fkl_pipeline_destroy(fkl_pipeline p);
+
+/* Message of the last failed call on this thread ("" if none). */
+FKL_API const char* fkl_last_error(void);
+
+/* ------------------------------------------------------------------------ */
+/* Unfused reference form (same GPU): one kernel per operation               */
+/* ------------------------------------------------------------------------ */
+
+/*
+ * The chain as a conventional library runs it (paper §II Fig. 3A, Algorithm
+ * 1 "MainFunctionA"): one kernel per operation, every intermediate written to
+ * and read back from device memory. It uses the same Operation code as the
+ * fused kernel, so results are identical to fkl_execute_batch.
+ *
+ * fkl_unfused_workspace_bytes: bytes of device workspace (for the
+ * intermediates of one image, reused image after image) that
+ * fkl_execute_batch_unfused needs for these arguments. This is also the
+ * device memory that fusion saves (paper §VI-L).
+ * fkl_execute_batch_unfused: `workspace` is caller-owned device memory of at
+ * least that size, 256-byte aligned. Launch count = n * (ops in the chain),
+ * except vertical chains (one launch per Mul/Add over the whole tensor).
+ */
+FKL_API fkl_status fkl_unfused_workspace_bytes(fkl_pipeline p, int32_t n,
+                                       const fkl_tensor* ins,
+                                       const int32_t* rois,
+                                       const fkl_tensor* out, size_t* bytes);
+FKL_API fkl_status fkl_execute_batch_unfused(fkl_pipeline p, int32_t n,
+                                     const fkl_tensor* ins, const int32_t* rois,
+                                     fkl_tensor* out, void* workspace,
+                                     size_t workspace_bytes, void* stream);
+
+/* ------------------------------------------------------------------------ */
+/* Introspection and tuning                                                 */
+/* ------------------------------------------------------------------------ */
+
+/* Name of the compiled kernel the pipeline is bound to; the string is owned
+ * by the pipeline and valid until fkl_pipeline_destroy. */
+FKL_API const char* fkl_pipeline_kernel_name(fkl_pipeline p);
+
+/* Launch shape used by the fused kernel: V output pixels (elements) per
+ * thread, a TX x TY thread block, RY rows per thread. */
+typedef struct {
+  int32_t vec;      /* pixels per thread along x: 4, 8 or 16              */
+  int32_t tx, ty;   /* threads per block along x and y (tx*ty <= 1024)   */
+  int32_t ry;       /* output rows per thread: 1 or 2                     */
+} fkl_launch_shape;
+
+/* Current / set the launch shape. fkl_pipeline_set_shape validates it
+ * (FKL_ERR_INVALID if the kernel has no instantiation for it). */
+FKL_API fkl_status fkl_pipeline_get_shape(fkl_pipeline p, fkl_launch_shape* shape);
+FKL_API fkl_status fkl_pipeline_set_shape(fkl_pipeline p, const fkl_launch_shape* shape);
+
+/* Number of launch shapes the autotuner may try for this pipeline, and the
+ * k-th of them (k in [0, count)). */
+FKL_API int32_t fkl_pipeline_shape_count(fkl_pipeline p);
+FKL_API fkl_status fkl_pipeline_shape_at(fkl_pipeline p, int32_t k,
+                                 fkl_launch_shape* shape);
+
+/* Library version string. */
+FKL_API const char* fkl_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* FKL_H_ */

@@ -1,0 +1,593 @@
+// The C ABI (include/fkl.h): chain parsing, argument validation, the table
+// of compiled chain families, and the launch of fused and unfused forms.
+#include <algorithm>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <mutex>
+#include <new>
+#include <string>
+
+#include "registry.h"
+
+struct fkl_pipeline_s {
+  fkl_impl::Spec spec;
+  fkl_launch_shape shape;
+  std::string name;
+};
+
+namespace fkl_impl {
+
+namespace {
+
+thread_local std::string t_error;
+
+fkl_status fail(fkl_status s, const char* fmt, ...) {
+  char buf[512];
+  va_list ap;
+  va_start(ap, fmt);
+  std::vsnprintf(buf, sizeof(buf), fmt, ap);
+  va_end(ap);
+  t_error = buf;
+  return s;
+}
+
+fkl_status cuda_fail(cudaError_t e, const char* what) {
+  return fail(FKL_ERR_CUDA, "%s: %s (%s)", what, cudaGetErrorName(e), cudaGetErrorString(e));
+}
+
+constexpr int kMaxDim = 16384;
+
+int dtype_bytes(int dt) {
+  switch (dt) {
+    case FKL_U8:
+    case FKL_E4M3:
+      return 1;
+    case FKL_F16:
+    case FKL_BF16:
+      return 2;
+    case FKL_F32:
+      return 4;
+    default:
+      return 0;
+  }
+}
+
+const char* dtype_name(int dt) {
+  switch (dt) {
+    case FKL_U8:
+      return "u8";
+    case FKL_F32:
+      return "f32";
+    case FKL_F16:
+      return "f16";
+    case FKL_BF16:
+      return "bf16";
+    case FKL_E4M3:
+      return "e4m3";
+    default:
+      return "?";
+  }
+}
+
+bool is_read(int op) { return op == FKL_OP_READ_U8C3 || op == FKL_OP_READ_NV12 || op == FKL_OP_READ_F32; }
+bool is_write(int op) { return op == FKL_OP_WRITE_PACKED || op == FKL_OP_WRITE_SPLIT; }
+bool is_modifier(int op) { return op == FKL_OP_CROP || op == FKL_OP_RESIZE || op == FKL_OP_LETTERBOX; }
+bool is_compute(int op) {
+  return op == FKL_OP_SWAP_RB || op == FKL_OP_MUL || op == FKL_OP_ADD || op == FKL_OP_SUB ||
+         op == FKL_OP_DIV || op == FKL_OP_ADD_SAT_U8;
+}
+
+// ROp -> COp* -> WOp grammar, then the compiled-family table.
+fkl_status parse(const fkl_op_desc* ops, int n, Spec& s) {
+  if (n < 2) return fail(FKL_ERR_INVALID, "a chain needs at least a read and a write op (got %d ops)", n);
+  const int src = ops[0].op;
+  const int wop = ops[n - 1].op;
+  if (!is_read(src)) return fail(FKL_ERR_INVALID, "op 0 must be a READ_* op (got code %d)", src);
+  if (!is_write(wop)) return fail(FKL_ERR_INVALID, "the last op must be a WRITE_* op (got code %d)", wop);
+  for (int k = 1; k < n - 1; ++k) {
+    const int op = ops[k].op;
+    if (is_read(op)) return fail(FKL_ERR_INVALID, "op %d: a read op may only come first", k);
+    if (is_write(op)) return fail(FKL_ERR_INVALID, "op %d: a write op may only come last", k);
+    if (!is_modifier(op) && !is_compute(op)) return fail(FKL_ERR_INVALID, "op %d: unknown op code %d", k, op);
+  }
+  const int odt = ops[n - 1].i[0];
+  if (dtype_bytes(odt) == 0) return fail(FKL_ERR_INVALID, "write op: unknown dtype %d", odt);
+  s.split = wop == FKL_OP_WRITE_SPLIT;
+  s.out_dtype = odt;
+  if (odt == FKL_E4M3) {
+    const float sc = ops[n - 1].f[0];
+    if (!(sc > 0.f) || !std::isfinite(sc))
+      return fail(FKL_ERR_INVALID, "E4M3 output needs a finite per-tensor scale > 0 in f[0]");
+    s.fp8_scale = sc;
+  }
+
+  if (src == FKL_OP_READ_F32) {
+    s.family = FAM_VCHAIN;
+    for (int k = 1; k < n - 1; ++k) {
+      const int op = ops[k].op;
+      if (op == FKL_OP_MUL || op == FKL_OP_ADD) {
+        s.vkinds.push_back(op == FKL_OP_ADD ? 1 : 0);
+        s.vconsts.push_back(ops[k].f[0]);
+      } else if (is_modifier(op)) {
+        return fail(FKL_ERR_INVALID, "op %d: read modifiers apply to image reads only", k);
+      } else {
+        return fail(FKL_ERR_UNSUPPORTED, "op %d: float32 tensor chains take MUL and ADD only", k);
+      }
+    }
+    if (wop != FKL_OP_WRITE_PACKED || odt != FKL_F32)
+      return fail(FKL_ERR_UNSUPPORTED, "float32 tensor chains write packed F32 only");
+    if (s.vkinds.size() > 65536) return fail(FKL_ERR_UNSUPPORTED, "vertical chains are limited to 65536 ops");
+    return FKL_OK;
+  }
+
+  int k = 1;
+  if (ops[k].op == FKL_OP_CROP) {
+    const int32_t* c = ops[k].i;
+    if (c[0] < 0 || c[1] < 0 || c[2] <= 0 || c[3] <= 0 || c[2] > kMaxDim || c[3] > kMaxDim)
+      return fail(FKL_ERR_INVALID, "CROP (%d,%d,%d,%d): need x, y >= 0 and 0 < w, h <= %d", c[0], c[1], c[2], c[3], kMaxDim);
+    s.has_crop = true;
+    std::memcpy(s.crop, c, sizeof(s.crop));
+    ++k;
+  }
+  if (ops[k].op == FKL_OP_RESIZE || ops[k].op == FKL_OP_LETTERBOX) {
+    s.geom = ops[k].op == FKL_OP_RESIZE ? GEOM_RESIZE : GEOM_LETTERBOX;
+    s.out_w = ops[k].i[0];
+    s.out_h = ops[k].i[1];
+    if (s.out_w <= 0 || s.out_h <= 0 || s.out_w > kMaxDim || s.out_h > kMaxDim)
+      return fail(FKL_ERR_INVALID, "RESIZE/LETTERBOX size %dx%d outside 1..%d", s.out_w, s.out_h, kMaxDim);
+    s.pad = s.geom == GEOM_LETTERBOX ? ops[k].f[0] : 0.f;
+    ++k;
+  }
+  int stage = 0;  // compiled order: SWAP_RB, MUL, ADD|SUB, DIV, ADD_SAT_U8
+  for (; k < n - 1; ++k) {
+    const fkl_op_desc& d = ops[k];
+    int want;
+    switch (d.op) {
+      case FKL_OP_SWAP_RB:
+        want = 1;
+        s.swap = true;
+        break;
+      case FKL_OP_MUL:
+        want = 2;
+        s.has_mul = true;
+        std::memcpy(s.mul, d.f, sizeof(s.mul));
+        break;
+      case FKL_OP_ADD:
+      case FKL_OP_SUB:
+        want = 3;
+        s.has_sub = true;
+        for (int c = 0; c < 3; ++c) s.sub[c] = d.op == FKL_OP_SUB ? d.f[c] : -d.f[c];
+        break;
+      case FKL_OP_DIV:
+        want = 4;
+        s.has_div = true;
+        std::memcpy(s.div, d.f, sizeof(s.div));
+        break;
+      case FKL_OP_ADD_SAT_U8:
+        want = 5;
+        s.has_addsat = true;
+        std::memcpy(s.addsat, d.i, sizeof(s.addsat));
+        break;
+      default:
+        return fail(FKL_ERR_INVALID, "op %d: read modifiers must directly follow the read op", k);
+    }
+    if (want <= stage)
+      return fail(FKL_ERR_UNSUPPORTED,
+                  "op %d: no compiled chain has this op order (compiled: SWAP_RB, MUL, ADD|SUB, DIV, ADD_SAT_U8)", k);
+    stage = want;
+  }
+  const bool float_ops = s.has_mul || s.has_sub || s.has_div;
+  if (s.has_addsat || odt == FKL_U8) {
+    if (src != FKL_OP_READ_U8C3 || s.geom != GEOM_NONE || float_ops || odt != FKL_U8)
+      return fail(FKL_ERR_UNSUPPORTED, "u8 chains are READ_U8C3 [CROP] [SWAP_RB] [ADD_SAT_U8] WRITE_* (U8)");
+    s.family = FAM_INT;
+    return FKL_OK;
+  }
+  s.family = src == FKL_OP_READ_U8C3 ? FAM_PACKED : FAM_NV12;
+  if (!s.split && odt != FKL_F32) return fail(FKL_ERR_UNSUPPORTED, "packed float outputs are F32 only");
+  return FKL_OK;
+}
+
+// ------------------------------------------------------------------ tensors
+
+struct OutDesc {
+  fkl::OutParams p;
+  int N, H, W;
+};
+
+fkl_status check_out(const Spec& s, const fkl_tensor* t, int n, OutDesc& o) {
+  if (!t || !t->data) return fail(FKL_ERR_INVALID, "output tensor missing");
+  if (t->dtype != s.out_dtype)
+    return fail(FKL_ERR_INVALID, "output dtype %s, chain writes %s", dtype_name(t->dtype), dtype_name(s.out_dtype));
+  const int B = dtype_bytes(s.out_dtype);
+  int64_t N, H, W, C;
+  if (s.split) {
+    if (t->layout != FKL_LAYOUT_NCHW) return fail(FKL_ERR_INVALID, "WRITE_SPLIT needs an NCHW output");
+    N = t->dims[0];
+    C = t->dims[1];
+    H = t->dims[2];
+    W = t->dims[3];
+  } else {
+    if (t->layout != FKL_LAYOUT_NHWC) return fail(FKL_ERR_INVALID, "WRITE_PACKED needs an NHWC output");
+    N = t->dims[0];
+    H = t->dims[1];
+    W = t->dims[2];
+    C = t->dims[3];
+  }
+  if (C != 3) return fail(FKL_ERR_INVALID, "output must have 3 channels (got %lld)", (long long)C);
+  if (N < n) return fail(FKL_ERR_INVALID, "output holds %lld images, batch has %d", (long long)N, n);
+  if (H <= 0 || W <= 0 || H > kMaxDim || W > kMaxDim)
+    return fail(FKL_ERR_INVALID, "output size %lldx%lld outside 1..%d", (long long)W, (long long)H, kMaxDim);
+  if (s.geom != GEOM_NONE && (H != s.out_h || W != s.out_w))
+    return fail(FKL_ERR_INVALID, "output is %lldx%lld, chain resizes to %dx%d", (long long)W, (long long)H, s.out_w, s.out_h);
+  const int64_t row = s.split ? W * B : W * 3 * B;
+  const int64_t pitch = t->pitch_bytes ? t->pitch_bytes : row;
+  if (pitch < row) return fail(FKL_ERR_INVALID, "output pitch %lld < row bytes %lld", (long long)pitch, (long long)row);
+  std::memset(&o, 0, sizeof(o));
+  o.p.base = static_cast<uint8_t*>(t->data);
+  o.p.pitch = pitch;
+  o.p.plane = H * pitch;
+  o.p.img = s.split ? 3 * H * pitch : H * pitch;
+  o.p.scale_inv = s.out_dtype == FKL_E4M3 ? static_cast<float>(1.0 / s.fp8_scale) : 1.f;
+  o.p.aligned = (reinterpret_cast<uintptr_t>(t->data) % 16 == 0 && pitch % 16 == 0) ? 1 : 0;
+  o.N = static_cast<int>(N);
+  o.H = static_cast<int>(H);
+  o.W = static_cast<int>(W);
+  return FKL_OK;
+}
+
+// Per-image ROp parameters from the input tensor, the ROI and the geometry.
+fkl_status image_params(const Spec& s, const fkl_tensor* t, const int32_t* roi_in, int i,
+                        const OutDesc& od, fkl::ResampleParams& r) {
+  if (!t || !t->data) return fail(FKL_ERR_INVALID, "input %d missing", i);
+  if (t->dtype != FKL_U8) return fail(FKL_ERR_INVALID, "input %d: image sources are U8", i);
+  int64_t H, W, row;
+  if (s.family == FAM_NV12) {
+    if (t->layout != FKL_LAYOUT_NV12) return fail(FKL_ERR_INVALID, "input %d: READ_NV12 needs an NV12 tensor", i);
+    H = t->dims[0];
+    W = t->dims[1];
+    if (H % 2 || W % 2) return fail(FKL_ERR_INVALID, "input %d: NV12 needs even width and height", i);
+    row = W;
+  } else {
+    if (t->layout != FKL_LAYOUT_HWC || t->dims[2] != 3)
+      return fail(FKL_ERR_INVALID, "input %d: READ_U8C3 needs an HWC tensor with 3 channels", i);
+    H = t->dims[0];
+    W = t->dims[1];
+    row = 3 * W;
+  }
+  if (H <= 0 || W <= 0 || H > kMaxDim || W > kMaxDim)
+    return fail(FKL_ERR_INVALID, "input %d: size %lldx%lld outside 1..%d", i, (long long)W, (long long)H, kMaxDim);
+  const int64_t pitch = t->pitch_bytes ? t->pitch_bytes : row;
+  if (pitch < row || pitch > (int64_t(1) << 30))
+    return fail(FKL_ERR_INVALID, "input %d: pitch %lld invalid for rows of %lld bytes", i, (long long)pitch, (long long)row);
+  int32_t roi[4] = {0, 0, static_cast<int32_t>(W), static_cast<int32_t>(H)};
+  if (roi_in) {
+    std::memcpy(roi, roi_in + 4 * i, sizeof(roi));
+  } else if (s.has_crop) {
+    std::memcpy(roi, s.crop, sizeof(roi));
+  }
+  if (roi[0] < 0 || roi[1] < 0 || roi[2] <= 0 || roi[3] <= 0 || roi[0] + int64_t(roi[2]) > W ||
+      roi[1] + int64_t(roi[3]) > H)
+    return fail(FKL_ERR_INVALID, "input %d: ROI (%d,%d,%d,%d) not inside the %lldx%lld image", i, roi[0], roi[1],
+                roi[2], roi[3], (long long)W, (long long)H);
+  std::memset(&r, 0, sizeof(r));
+  r.src = static_cast<const uint8_t*>(t->data);
+  r.uv = s.family == FAM_NV12 ? r.src + H * pitch : nullptr;
+  r.pitch = static_cast<int32_t>(pitch);
+  r.rx = roi[0];
+  r.ry = roi[1];
+  r.rw = roi[2];
+  r.rh = roi[3];
+  if (s.geom == GEOM_NONE) {
+    if (r.rw != od.W || r.rh != od.H)
+      return fail(FKL_ERR_INVALID, "input %d: ROI %dx%d must equal the %dx%d output when the chain has no resize", i,
+                  r.rw, r.rh, od.W, od.H);
+    r.dw = r.rw;
+    r.dh = r.rh;
+  } else if (s.geom == GEOM_RESIZE) {
+    r.dw = od.W;
+    r.dh = od.H;
+  } else {
+    const double sc = std::min(static_cast<double>(od.W) / r.rw, static_cast<double>(od.H) / r.rh);
+    r.dw = std::max(1, std::min(od.W, static_cast<int>(std::floor(r.rw * sc + 0.5))));
+    r.dh = std::max(1, std::min(od.H, static_cast<int>(std::floor(r.rh * sc + 0.5))));
+    r.ox = (od.W - r.dw) / 2;
+    r.oy = (od.H - r.dh) / 2;
+  }
+  r.pad = s.pad;
+  r.inv_area = static_cast<float>(1.0 / (4.0 * r.dw * r.dh));
+  if (s.family == FAM_NV12 && r.rw == 2 * r.dw && r.rh == 2 * r.dh && r.rx % 16 == 0 && r.ry % 2 == 0 &&
+      pitch % 16 == 0 && reinterpret_cast<uintptr_t>(r.src) % 16 == 0)
+    r.flags |= fkl::kFast2x;
+  return FKL_OK;
+}
+
+std::mutex g_sm_mu;
+int g_sm[64] = {0};
+
+}  // namespace
+
+int sm_count() {
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return 152;
+  std::lock_guard<std::mutex> lk(g_sm_mu);
+  if (g_sm[dev] == 0) {
+    int v = 0;
+    if (cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || v <= 0) v = 152;
+    g_sm[dev] = v;
+  }
+  return g_sm[dev];
+}
+
+namespace {
+const int kBlocks[][2] = {{8, 16}, {16, 8}, {16, 16}, {32, 4}, {32, 8}, {64, 2}, {64, 4}, {128, 1}, {128, 2}};
+}
+
+std::vector<fkl_launch_shape> shapes_for(const Spec& s) {
+  std::vector<int> vecs;
+  if (s.family == FAM_INT) {
+    vecs = {16};
+  } else if (s.family == FAM_PACKED || s.family == FAM_NV12) {
+    if (s.out_dtype == FKL_F32)
+      vecs = s.split ? std::vector<int>{4, 8} : std::vector<int>{4};
+    else
+      vecs = {8, 16};
+  } else {
+    return {};
+  }
+  std::vector<fkl_launch_shape> out;
+  for (int v : vecs)
+    for (int ry : {1, 2}) {
+      if (v > 8 && ry > 1) continue;  // not compiled (register budget)
+      for (const auto& b : kBlocks) out.push_back(fkl_launch_shape{v, b[0], b[1], ry});
+    }
+  return out;
+}
+
+fkl_launch_shape default_shape(const Spec& s) {
+  if (s.family == FAM_INT) return {16, 16, 8, 1};
+  if (s.family == FAM_VCHAIN) return {16, 256, 1, 1};
+  return {s.out_dtype == FKL_F32 ? 4 : 8, 16, 8, 1};
+}
+
+}  // namespace fkl_impl
+
+using namespace fkl_impl;
+
+namespace {
+
+std::string make_name(const Spec& s) {
+  std::string n = "fused:";
+  switch (s.family) {
+    case FAM_PACKED:
+      n += "ResizeU8C3";
+      break;
+    case FAM_NV12:
+      n += "ResizeNV12";
+      break;
+    case FAM_INT:
+      n += "CropU8C3";
+      break;
+    case FAM_VCHAIN:
+      n += "ReadF32";
+      break;
+  }
+  if (s.family == FAM_VCHAIN) {
+    n += ">(Mul|Add)x" + std::to_string(s.vkinds.size()) + ">WriteF32";
+    return n;
+  }
+  if (s.swap) n += ">SwapRB";
+  if (s.family == FAM_INT) {
+    n += ">AddSatU8>WriteU8";
+  } else {
+    n += ">Mul>Sub>Div";
+    n += s.split ? ">WriteSplit<" : ">WritePacked<";
+    n += dtype_name(s.out_dtype);
+    n += ">";
+  }
+  return n;
+}
+
+cudaError_t launch_family(const LaunchCtx& c) {
+  const Spec& s = *c.spec;
+  if (s.family == FAM_INT) return launch_int(c);
+  const bool packed = s.family == FAM_PACKED;
+  switch (s.out_dtype) {
+    case FKL_F32:
+      return packed ? launch_packed_f32(c) : launch_nv12_f32(c);
+    case FKL_F16:
+      return packed ? launch_packed_f16(c) : launch_nv12_f16(c);
+    case FKL_BF16:
+      return packed ? launch_packed_bf16(c) : launch_nv12_bf16(c);
+    case FKL_E4M3:
+      return packed ? launch_packed_e4m3(c) : launch_nv12_e4m3(c);
+    default:
+      return cudaErrorInvalidValue;
+  }
+}
+
+fkl_status check_linear(const fkl_tensor* in, const fkl_tensor* out, int64_t& n) {
+  if (!in || !out || !in->data || !out->data) return fail(FKL_ERR_INVALID, "tensor missing");
+  if (in->layout != FKL_LAYOUT_LINEAR || out->layout != FKL_LAYOUT_LINEAR || in->dtype != FKL_F32 ||
+      out->dtype != FKL_F32)
+    return fail(FKL_ERR_INVALID, "float32 tensor chains need LINEAR F32 input and output");
+  if (in->dims[0] != out->dims[0] || in->dims[0] < 0)
+    return fail(FKL_ERR_INVALID, "input and output lengths differ (%lld vs %lld)", (long long)in->dims[0],
+                (long long)out->dims[0]);
+  n = in->dims[0];
+  return FKL_OK;
+}
+
+fkl_status validate_batch(const fkl_pipeline p, int32_t n, const fkl_tensor* ins, const int32_t* rois,
+                          const fkl_tensor* out, OutDesc& od, std::vector<fkl::ResampleParams>& imgs) {
+  if (!p) return fail(FKL_ERR_INVALID, "null pipeline");
+  if (p->spec.family == FAM_VCHAIN) return fail(FKL_ERR_INVALID, "float32 tensor chains run through fkl_execute");
+  if (n < 0) return fail(FKL_ERR_INVALID, "negative batch size");
+  if (n > 0 && !ins) return fail(FKL_ERR_INVALID, "inputs missing");
+  fkl_status st = check_out(p->spec, out, n, od);
+  if (st != FKL_OK) return st;
+  try {
+    imgs.resize(n);
+  } catch (...) {
+    return fail(FKL_ERR_OOM, "host allocation failed");
+  }
+  for (int i = 0; i < n; ++i) {
+    st = image_params(p->spec, &ins[i], rois, i, od, imgs[i]);
+    if (st != FKL_OK) return st;
+  }
+  return FKL_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+fkl_status fkl_pipeline_create(const fkl_op_desc* ops, int32_t n_ops, fkl_pipeline* out) {
+  if (!out) return fail(FKL_ERR_INVALID, "out is NULL");
+  *out = nullptr;
+  if (!ops) return fail(FKL_ERR_INVALID, "ops is NULL");
+  Spec s;
+  try {
+    const fkl_status st = parse(ops, n_ops, s);
+    if (st != FKL_OK) return st;
+    auto* p = new (std::nothrow) fkl_pipeline_s;
+    if (!p) return fail(FKL_ERR_OOM, "host allocation failed");
+    p->spec = std::move(s);
+    p->shape = default_shape(p->spec);
+    p->name = make_name(p->spec);
+    *out = p;
+  } catch (const std::bad_alloc&) {
+    return fail(FKL_ERR_OOM, "host allocation failed");
+  }
+  return FKL_OK;
+}
+
+void fkl_pipeline_destroy(fkl_pipeline p) { delete p; }
+
+const char* fkl_last_error(void) { return t_error.c_str(); }
+
+const char* fkl_version(void) { return "fkl-gb300 0.1 (sm_103a)"; }
+
+const char* fkl_pipeline_kernel_name(fkl_pipeline p) { return p ? p->name.c_str() : ""; }
+
+fkl_status fkl_execute_batch(fkl_pipeline p, int32_t n, const fkl_tensor* ins, const int32_t* rois,
+                             fkl_tensor* out, void* stream) {
+  OutDesc od;
+  std::vector<fkl::ResampleParams> imgs;
+  fkl_status st = validate_batch(p, n, ins, rois, out, od, imgs);
+  if (st != FKL_OK) return st;
+  for (int start = 0; start < n; start += kBatchCap) {
+    LaunchCtx c;
+    c.spec = &p->spec;
+    c.shape = p->shape;
+    c.imgs = imgs.data() + start;
+    c.n = std::min(kBatchCap, n - start);
+    c.out = od.p;
+    c.out.base += start * od.p.img;
+    c.H = od.H;
+    c.W = od.W;
+    c.stream = static_cast<cudaStream_t>(stream);
+    const cudaError_t e = launch_family(c);
+    if (e != cudaSuccess) return cuda_fail(e, "fused kernel launch");
+  }
+  return FKL_OK;
+}
+
+fkl_status fkl_execute(fkl_pipeline p, const fkl_tensor* in, fkl_tensor* out, void* stream) {
+  if (!p) return fail(FKL_ERR_INVALID, "null pipeline");
+  if (p->spec.family == FAM_VCHAIN) {
+    int64_t n = 0;
+    const fkl_status st = check_linear(in, out, n);
+    if (st != FKL_OK) return st;
+    if (n == 0) return FKL_OK;
+    const cudaError_t e = launch_vchain(p->spec, static_cast<const float*>(in->data), static_cast<float*>(out->data),
+                                        n, static_cast<cudaStream_t>(stream));
+    return e == cudaSuccess ? FKL_OK : cuda_fail(e, "vertical chain launch");
+  }
+  return fkl_execute_batch(p, 1, in, nullptr, out, stream);
+}
+
+fkl_status fkl_unfused_workspace_bytes(fkl_pipeline p, int32_t n, const fkl_tensor* ins, const int32_t* rois,
+                                       const fkl_tensor* out, size_t* bytes) {
+  if (!bytes) return fail(FKL_ERR_INVALID, "bytes is NULL");
+  *bytes = 0;
+  if (!p) return fail(FKL_ERR_INVALID, "null pipeline");
+  if (p->spec.family == FAM_VCHAIN) return FKL_OK;
+  OutDesc od;
+  std::vector<fkl::ResampleParams> imgs;
+  const fkl_status st = validate_batch(p, n, ins, rois, out, od, imgs);
+  if (st != FKL_OK) return st;
+  const int64_t elem = p->spec.family == FAM_INT ? 3 : 12;
+  int64_t need = static_cast<int64_t>(od.H) * od.W;
+  if (p->spec.family == FAM_NV12)
+    for (const auto& r : imgs) need = std::max<int64_t>(need, static_cast<int64_t>(r.rw) * r.rh);
+  const int64_t each = (need * elem + 255) / 256 * 256;
+  *bytes = static_cast<size_t>(2 * each);
+  return FKL_OK;
+}
+
+fkl_status fkl_execute_batch_unfused(fkl_pipeline p, int32_t n, const fkl_tensor* ins, const int32_t* rois,
+                                     fkl_tensor* out, void* workspace, size_t workspace_bytes, void* stream) {
+  if (!p) return fail(FKL_ERR_INVALID, "null pipeline");
+  const cudaStream_t s = static_cast<cudaStream_t>(stream);
+  if (p->spec.family == FAM_VCHAIN) {
+    if (n != 1) return fail(FKL_ERR_INVALID, "float32 tensor chains take one tensor (n = 1)");
+    int64_t len = 0;
+    const fkl_status st = check_linear(ins, out, len);
+    if (st != FKL_OK) return st;
+    if (len == 0) return FKL_OK;
+    const cudaError_t e = launch_unfused_vchain(p->spec, static_cast<const float*>(ins->data),
+                                                static_cast<float*>(out->data), len, s);
+    return e == cudaSuccess ? FKL_OK : cuda_fail(e, "unfused launch");
+  }
+  size_t need = 0;
+  fkl_status st = fkl_unfused_workspace_bytes(p, n, ins, rois, out, &need);
+  if (st != FKL_OK) return st;
+  if (!workspace || workspace_bytes < need || reinterpret_cast<uintptr_t>(workspace) % 256)
+    return fail(FKL_ERR_INVALID, "workspace must be >= %zu bytes and 256-byte aligned", need);
+  OutDesc od;
+  std::vector<fkl::ResampleParams> imgs;
+  st = validate_batch(p, n, ins, rois, out, od, imgs);
+  if (st != FKL_OK) return st;
+  uint8_t* ws0 = static_cast<uint8_t*>(workspace);
+  uint8_t* ws1 = ws0 + need / 2;
+  for (int i = 0; i < n; ++i) {
+    const cudaError_t e = launch_unfused_image(p->spec, imgs[i], od.p, i, od.H, od.W, ws0, ws1, s);
+    if (e != cudaSuccess) return cuda_fail(e, "unfused launch");
+  }
+  return FKL_OK;
+}
+
+fkl_status fkl_pipeline_get_shape(fkl_pipeline p, fkl_launch_shape* shape) {
+  if (!p || !shape) return fail(FKL_ERR_INVALID, "null argument");
+  *shape = p->shape;
+  return FKL_OK;
+}
+
+fkl_status fkl_pipeline_set_shape(fkl_pipeline p, const fkl_launch_shape* shape) {
+  if (!p || !shape) return fail(FKL_ERR_INVALID, "null argument");
+  for (const auto& c : shapes_for(p->spec)) {
+    if (c.vec == shape->vec && c.tx == shape->tx && c.ty == shape->ty && c.ry == shape->ry) {
+      p->shape = *shape;
+      return FKL_OK;
+    }
+  }
+  return fail(FKL_ERR_INVALID, "no compiled launch shape vec=%d block=%dx%d ry=%d for this chain", shape->vec,
+              shape->tx, shape->ty, shape->ry);
+}
+
+int32_t fkl_pipeline_shape_count(fkl_pipeline p) {
+  return p ? static_cast<int32_t>(shapes_for(p->spec).size()) : 0;
+}
+
+fkl_status fkl_pipeline_shape_at(fkl_pipeline p, int32_t k, fkl_launch_shape* shape) {
+  if (!p || !shape) return fail(FKL_ERR_INVALID, "null argument");
+  const auto v = shapes_for(p->spec);
+  if (k < 0 || k >= static_cast<int32_t>(v.size())) return fail(FKL_ERR_INVALID, "shape index %d out of range", k);
+  *shape = v[k];
+  return FKL_OK;
+}
+
+}  // extern "C"

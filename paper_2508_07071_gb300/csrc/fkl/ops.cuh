@@ -1,0 +1,614 @@
+// Operations of the preprocessing chains: Read (K1), Compute (K2) and Write
+// (K3) steps of paper Fig. 3, in the exec forms of paper Table I.
+//
+// Every floating-point step is written with an explicit rounding intrinsic
+// (__fmul_rn, __fadd_rn, __fdiv_rn, ...), so the compiler cannot contract or
+// reassociate across Ops. The same Op therefore gives the same bits whether
+// it runs inside one fused kernel or alone in a kernel of its own, which is
+// what lets the unfused reference form be compared bit for bit.
+#pragma once
+
+#include "core.cuh"
+
+namespace fkl {
+
+// ===========================================================================
+// Geometry shared by the resampling Read Operations
+// ===========================================================================
+
+// Per-image parameters of a resampling ROp. The source window (rx, ry, rw,
+// rh) is resized to dw x dh and placed at (ox, oy) in the output; output
+// pixels outside the placed window read `pad` (letterbox). A plain resize is
+// ox = oy = 0 and dw x dh = the output size; a plain crop is dw = rw, dh = rh.
+struct ResampleParams {
+  const uint8_t* src;  // packed image base, or NV12 luma plane
+  const uint8_t* uv;   // NV12 chroma plane (nullptr otherwise)
+  int32_t pitch;       // bytes per source row (both NV12 planes)
+  int32_t rx, ry, rw, rh;
+  int32_t ox, oy, dw, dh;
+  float pad;
+  float inv_area;      // fl32(1 / (4 dw dh)), integer-weight bilinear
+  int32_t flags;       // kFast2x: exact 2x downscale, rows 16-byte aligned
+};
+static_assert(sizeof(ResampleParams) == 64, "kernel-parameter table entry");
+
+constexpr int32_t kFast2x = 1;
+
+// Half-pixel sample along one axis for output index d (0 <= d < n_dst):
+// u = (d + 1/2) n_src / n_dst - 1/2 = num / D with num = (2d+1) n_src - n_dst
+// and D = 2 n_dst, clamped to [0, n_src - 1]. i0 = floor(u), i1 = min(i0 + 1,
+// n_src - 1) and the weight of i1 is w1 / D, all in exact integers.
+struct AxisTap {
+  int i0;
+  int i1;
+  int w1;  // in units of 1/D
+};
+
+// Walks the taps of consecutive outputs d, d+1, ... with one division.
+struct AxisWalker {
+  int q, r;    // floor(num / D), num mod D of the current output
+  int qs, rs;  // divmod of the step 2 n_src by D
+  int D, n_src;
+
+  FKL_D AxisWalker(int d, int n_src_, int n_dst) {
+    n_src = n_src_;
+    D = 2 * n_dst;
+    const int num = (2 * d + 1) * n_src - n_dst;  // > -D for every d >= 0
+    const int shifted = num + D;                  // > 0
+    q = shifted / D - 1;
+    r = shifted - (q + 1) * D;
+    qs = (2 * n_src) / D;
+    rs = 2 * n_src - qs * D;
+  }
+  FKL_D AxisTap tap() const {
+    AxisTap t;
+    if (q < 0) {
+      t.i0 = 0;
+      t.w1 = 0;
+    } else if (q >= n_src - 1) {
+      t.i0 = n_src - 1;
+      t.w1 = 0;
+    } else {
+      t.i0 = q;
+      t.w1 = r;
+    }
+    t.i1 = min(t.i0 + 1, n_src - 1);
+    return t;
+  }
+  FKL_D void next() {
+    q += qs;
+    r += rs;
+    if (r >= D) {
+      r -= D;
+      q += 1;
+    }
+  }
+};
+
+// Bilinear blend of four float taps with weights w / D computed by IEEE
+// division (exact whenever the ratio is representable, e.g. 1/2).
+FKL_D F3 blend_float(const F3& t00, const F3& t01, const F3& t10, const F3& t11,
+                     const AxisTap& tx, int Dx, const AxisTap& ty, int Dy) {
+  const float ax1 = __fdiv_rn(static_cast<float>(tx.w1), static_cast<float>(Dx));
+  const float ax0 = __fdiv_rn(static_cast<float>(Dx - tx.w1), static_cast<float>(Dx));
+  const float ay1 = __fdiv_rn(static_cast<float>(ty.w1), static_cast<float>(Dy));
+  const float ay0 = __fdiv_rn(static_cast<float>(Dy - ty.w1), static_cast<float>(Dy));
+  F3 o;
+#pragma unroll
+  for (int c = 0; c < 3; ++c) {
+    const float top = __fadd_rn(__fmul_rn(ax0, t00.v[c]), __fmul_rn(ax1, t01.v[c]));
+    const float bot = __fadd_rn(__fmul_rn(ax0, t10.v[c]), __fmul_rn(ax1, t11.v[c]));
+    o.v[c] = __fadd_rn(__fmul_rn(ay0, top), __fmul_rn(ay1, bot));
+  }
+  return o;
+}
+
+// ===========================================================================
+// Read Operations
+// ===========================================================================
+
+// Packed 3-channel u8 image, crop window, bilinear resize and placement.
+// The four taps are u8 integers, so the blend is done exactly in integers:
+// N = (Dy - wy)((Dx - wx) S00 + wx S01) + wy((Dx - wx) S10 + wx S11) and the
+// value is N / (Dx Dy) with a single float conversion and one multiply.
+struct ResizeU8C3 {
+  using InstanceType = ReadType;
+  using ParamsType = ResampleParams;
+  using OutputType = F3;
+
+  static FKL_D F3 blend(const uint8_t* row0, const uint8_t* row1, const AxisTap& tx,
+                        int Dx, const AxisTap& ty, int Dy, float inv_area) {
+    const uint8_t* p00 = row0 + 3 * tx.i0;
+    const uint8_t* p01 = row0 + 3 * tx.i1;
+    const uint8_t* p10 = row1 + 3 * tx.i0;
+    const uint8_t* p11 = row1 + 3 * tx.i1;
+    const uint32_t wx1 = static_cast<uint32_t>(tx.w1);
+    const uint32_t wx0 = static_cast<uint32_t>(Dx - tx.w1);
+    const uint32_t wy1 = static_cast<uint32_t>(ty.w1);
+    const uint32_t wy0 = static_cast<uint32_t>(Dy - ty.w1);
+    F3 o;
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+      const uint32_t top = wx0 * __ldg(p00 + c) + wx1 * __ldg(p01 + c);
+      const uint32_t bot = wx0 * __ldg(p10 + c) + wx1 * __ldg(p11 + c);
+      const uint64_t n = static_cast<uint64_t>(wy0) * top + static_cast<uint64_t>(wy1) * bot;
+      o.v[c] = __fmul_rn(__ull2float_rn(n), inv_area);
+    }
+    return o;
+  }
+
+  static FKL_D F3 exec(const Point& pt, const ParamsType& p) {
+    const int lx = pt.x - p.ox, ly = pt.y - p.oy;
+    if (lx < 0 || ly < 0 || lx >= p.dw || ly >= p.dh) return F3{{p.pad, p.pad, p.pad}};
+    const AxisTap tx = AxisWalker(lx, p.rw, p.dw).tap();
+    const AxisTap ty = AxisWalker(ly, p.rh, p.dh).tap();
+    const uint8_t* base = p.src + static_cast<int64_t>(p.ry) * p.pitch + 3 * p.rx;
+    return blend(base + static_cast<int64_t>(ty.i0) * p.pitch,
+                 base + static_cast<int64_t>(ty.i1) * p.pitch, tx, 2 * p.dw, ty, 2 * p.dh,
+                 p.inv_area);
+  }
+
+  // V consecutive outputs of one row: the row taps are found once and the
+  // column taps by an incremental walk.
+  template <int V>
+  static FKL_D void exec_span(const Point& pt, const ParamsType& p, F3 (&out)[V]) {
+    const int lx = pt.x - p.ox, ly = pt.y - p.oy;
+    if (ly < 0 || ly >= p.dh || lx < 0 || lx + V > p.dw) {
+#pragma unroll
+      for (int k = 0; k < V; ++k) out[k] = exec(Point{pt.x + k, pt.y, pt.z}, p);
+      return;
+    }
+    const AxisTap ty = AxisWalker(ly, p.rh, p.dh).tap();
+    const uint8_t* base = p.src + static_cast<int64_t>(p.ry) * p.pitch + 3 * p.rx;
+    const uint8_t* row0 = base + static_cast<int64_t>(ty.i0) * p.pitch;
+    const uint8_t* row1 = base + static_cast<int64_t>(ty.i1) * p.pitch;
+    AxisWalker wx(lx, p.rw, p.dw);
+#pragma unroll
+    for (int k = 0; k < V; ++k) {
+      out[k] = blend(row0, row1, wx.tap(), 2 * p.dw, ty, 2 * p.dh, p.inv_area);
+      wx.next();
+    }
+  }
+};
+
+// BT.601 limited-range decode constants, divided by 255 so that the clamp to
+// [0, 255] becomes the free [0, 1] saturation of an add:
+//   R = 255 sat(Y'/219 + (1 - Kr) V' / 112), B = 255 sat(Y'/219 + (1 - Kb) U' / 112),
+//   G = 255 sat(Y'/219 - (1 - Kb)(Kb/Kg) U'/112 - (1 - Kr)(Kr/Kg) V'/112),
+// Kr = 0.299, Kb = 0.114, Kg = 1 - Kr - Kb, Y' = Y - 16, U' = U - 128, V' = V - 128.
+struct Bt601 {
+  static constexpr double kr = 0.299, kb = 0.114, kg = 1.0 - kr - kb;
+  static constexpr float cy = static_cast<float>(1.0 / 219.0);
+  static constexpr float crv = static_cast<float>((1.0 - kr) / 112.0);
+  static constexpr float cbu = static_cast<float>((1.0 - kb) / 112.0);
+  static constexpr float cgu = static_cast<float>((1.0 - kb) * kb / kg / 112.0);
+  static constexpr float cgv = static_cast<float>((1.0 - kr) * kr / kg / 112.0);
+};
+
+FKL_D float add_sat(float a, float b) {
+  float d;
+  asm("add.rn.sat.f32 %0, %1, %2;" : "=f"(d) : "f"(a), "f"(b));
+  return d;
+}
+FKL_D float sub_sat(float a, float b) {
+  float d;
+  asm("sub.rn.sat.f32 %0, %1, %2;" : "=f"(d) : "f"(a), "f"(b));
+  return d;
+}
+
+// Chroma terms of one (U, V) sample, shared by the luma samples that use it.
+struct ChromaTerms {
+  float rv, guv, bu;
+};
+FKL_D ChromaTerms chroma_terms(float uf, float vf) {
+  ChromaTerms t;
+  t.rv = __fmul_rn(Bt601::crv, vf);
+  t.guv = __fmaf_rn(Bt601::cgu, uf, __fmul_rn(Bt601::cgv, vf));
+  t.bu = __fmul_rn(Bt601::cbu, uf);
+  return t;
+}
+// RGB (0..255) of one luma sample yf = Y - 16 with its chroma terms.
+FKL_D F3 yuv_to_rgb(float yf, const ChromaTerms& t) {
+  const float l = __fmul_rn(Bt601::cy, yf);
+  F3 o;
+  o.v[0] = __fmul_rn(add_sat(l, t.rv), 255.f);
+  o.v[1] = __fmul_rn(sub_sat(l, t.guv), 255.f);
+  o.v[2] = __fmul_rn(add_sat(l, t.bu), 255.f);
+  return o;
+}
+
+// Byte k of a 32-bit word as an exact float minus `bias`: the byte is placed
+// in the mantissa of 2^23 and the 2^23 is subtracted along with the bias.
+FKL_D float byte_minus(uint32_t w, int k, float bias_plus_2p23) {
+  const uint32_t f = __byte_perm(w, 0x4B000000u, 0x7440u | static_cast<uint32_t>(k));
+  return __fsub_rn(__uint_as_float(f), bias_plus_2p23);
+}
+constexpr float k2p23 = 8388608.f;
+
+// One decoded NV12 sample at absolute source coordinates (sx, sy): nearest
+// (co-sited) chroma sample (sx/2, sy/2), U then V.
+FKL_D F3 nv12_sample(const ResampleParams& p, int sx, int sy) {
+  const float yf = static_cast<float>(__ldg(p.src + static_cast<int64_t>(sy) * p.pitch + sx)) - 16.f;
+  const uint8_t* c = p.uv + static_cast<int64_t>(sy >> 1) * p.pitch + (sx & ~1);
+  const float uf = static_cast<float>(__ldg(c)) - 128.f;
+  const float vf = static_cast<float>(__ldg(c + 1)) - 128.f;
+  return yuv_to_rgb(yf, chroma_terms(uf, vf));
+}
+
+// NV12 frame -> BT.601 RGB -> crop window -> bilinear resize -> placement.
+// Every tap is decoded (and clamped) first, then interpolated ("YUV->RGB,
+// then resize" order).
+struct ResizeNV12 {
+  using InstanceType = ReadType;
+  using ParamsType = ResampleParams;
+  using OutputType = F3;
+
+  static FKL_D F3 exec(const Point& pt, const ParamsType& p) {
+    const int lx = pt.x - p.ox, ly = pt.y - p.oy;
+    if (lx < 0 || ly < 0 || lx >= p.dw || ly >= p.dh) return F3{{p.pad, p.pad, p.pad}};
+    const AxisTap tx = AxisWalker(lx, p.rw, p.dw).tap();
+    const AxisTap ty = AxisWalker(ly, p.rh, p.dh).tap();
+    const F3 t00 = nv12_sample(p, p.rx + tx.i0, p.ry + ty.i0);
+    const F3 t01 = nv12_sample(p, p.rx + tx.i1, p.ry + ty.i0);
+    const F3 t10 = nv12_sample(p, p.rx + tx.i0, p.ry + ty.i1);
+    const F3 t11 = nv12_sample(p, p.rx + tx.i1, p.ry + ty.i1);
+    return blend_float(t00, t01, t10, t11, tx, 2 * p.dw, ty, 2 * p.dh);
+  }
+
+  // Exact 2x downscale of an even-aligned window: output k of the span is
+  // the mean of the 2x2 block that shares chroma sample k, so the span reads
+  // 2V luma bytes from each of two rows and 2V chroma bytes, all as 16-byte
+  // vectors. The result equals exec() bit for bit: with weights 1/2 the
+  // blend is fl(fl(t00 + t01) + fl(t10 + t11)) / 4.
+  template <int V>
+  static FKL_D void span_fast2x(const ParamsType& p, int lx, int ly, F3 (&out)[V]) {
+    static_assert(V % 8 == 0, "2x path reads 16-byte vectors");
+    constexpr int W = V / 8;  // uint4 per row
+    const int64_t y0 = p.ry + 2 * ly;
+    const uint4* r0 = reinterpret_cast<const uint4*>(p.src + y0 * p.pitch + p.rx + 2 * lx);
+    const uint4* r1 = reinterpret_cast<const uint4*>(p.src + (y0 + 1) * p.pitch + p.rx + 2 * lx);
+    const uint4* rc = reinterpret_cast<const uint4*>(p.uv + (y0 >> 1) * p.pitch + p.rx + 2 * lx);
+    uint4 a[W], b[W], c[W];
+#pragma unroll
+    for (int i = 0; i < W; ++i) {
+      a[i] = __ldg(r0 + i);
+      b[i] = __ldg(r1 + i);
+      c[i] = __ldg(rc + i);
+    }
+#pragma unroll
+    for (int k = 0; k < V; ++k) {
+      // output k uses bytes 2k, 2k+1 of each row: word (2k)/4 = k/2 of the
+      // 16-byte vector k/8, bytes (2k)%4 and (2k)%4 + 1.
+      const int vi = k / 8, wi = (k % 8) / 2, bi = (2 * k) % 4;
+      const uint32_t wa = reinterpret_cast<const uint32_t*>(&a[vi])[wi];
+      const uint32_t wb = reinterpret_cast<const uint32_t*>(&b[vi])[wi];
+      const uint32_t wc = reinterpret_cast<const uint32_t*>(&c[vi])[wi];
+      const ChromaTerms ct =
+          chroma_terms(byte_minus(wc, bi, k2p23 + 128.f), byte_minus(wc, bi + 1, k2p23 + 128.f));
+      const F3 t00 = yuv_to_rgb(byte_minus(wa, bi, k2p23 + 16.f), ct);
+      const F3 t01 = yuv_to_rgb(byte_minus(wa, bi + 1, k2p23 + 16.f), ct);
+      const F3 t10 = yuv_to_rgb(byte_minus(wb, bi, k2p23 + 16.f), ct);
+      const F3 t11 = yuv_to_rgb(byte_minus(wb, bi + 1, k2p23 + 16.f), ct);
+#pragma unroll
+      for (int ch = 0; ch < 3; ++ch) {
+        const float s = __fadd_rn(__fadd_rn(t00.v[ch], t01.v[ch]), __fadd_rn(t10.v[ch], t11.v[ch]));
+        out[k].v[ch] = __fmul_rn(s, 0.25f);
+      }
+    }
+  }
+
+  template <int V>
+  static FKL_D void exec_span(const Point& pt, const ParamsType& p, F3 (&out)[V]) {
+    const int lx = pt.x - p.ox, ly = pt.y - p.oy;
+    if (ly < 0 || ly >= p.dh) {  // whole span in the letterbox band
+#pragma unroll
+      for (int k = 0; k < V; ++k) out[k] = F3{{p.pad, p.pad, p.pad}};
+      return;
+    }
+    if constexpr (V % 8 == 0) {
+      if ((p.flags & kFast2x) && lx >= 0 && lx + V <= p.dw && ((2 * lx) & 15) == 0) {
+        span_fast2x<V>(p, lx, ly, out);
+        return;
+      }
+    }
+#pragma unroll
+    for (int k = 0; k < V; ++k) out[k] = exec(Point{pt.x + k, pt.y, pt.z}, p);
+  }
+};
+
+// NV12 decode at full resolution (the first kernel of the unfused NV12 chain).
+struct DecodeNV12 {
+  using InstanceType = ReadType;
+  using ParamsType = ResampleParams;
+  using OutputType = F3;
+  static FKL_D F3 exec(const Point& pt, const ParamsType& p) {
+    return nv12_sample(p, p.rx + pt.x, p.ry + pt.y);
+  }
+};
+
+// Packed float32 3-channel image (an intermediate of the unfused chains),
+// read through the same resampling geometry with float taps.
+struct ResizeF32C3 {
+  using InstanceType = ReadType;
+  using ParamsType = ResampleParams;
+  using OutputType = F3;
+  static FKL_D F3 load(const ParamsType& p, int sx, int sy) {
+    const float* q = reinterpret_cast<const float*>(p.src + static_cast<int64_t>(sy) * p.pitch) + 3 * sx;
+    return F3{{__ldg(q), __ldg(q + 1), __ldg(q + 2)}};
+  }
+  static FKL_D F3 exec(const Point& pt, const ParamsType& p) {
+    const int lx = pt.x - p.ox, ly = pt.y - p.oy;
+    if (lx < 0 || ly < 0 || lx >= p.dw || ly >= p.dh) return F3{{p.pad, p.pad, p.pad}};
+    const AxisTap tx = AxisWalker(lx, p.rw, p.dw).tap();
+    const AxisTap ty = AxisWalker(ly, p.rh, p.dh).tap();
+    return blend_float(load(p, p.rx + tx.i0, p.ry + ty.i0), load(p, p.rx + tx.i1, p.ry + ty.i0),
+                       load(p, p.rx + tx.i0, p.ry + ty.i1), load(p, p.rx + tx.i1, p.ry + ty.i1),
+                       tx, 2 * p.dw, ty, 2 * p.dh);
+  }
+};
+
+// Packed float32 3-channel image, pixel for pixel (unfused per-op kernels).
+struct ReadF32C3 {
+  using InstanceType = ReadType;
+  using ParamsType = ResampleParams;
+  using OutputType = F3;
+  static FKL_D F3 exec(const Point& pt, const ParamsType& p) {
+    return ResizeF32C3::load(p, p.rx + pt.x, p.ry + pt.y);
+  }
+};
+
+// Packed u8 3-channel crop (integer chains): no resampling.
+struct CropU8C3 {
+  using InstanceType = ReadType;
+  using ParamsType = ResampleParams;
+  using OutputType = U3;
+  static FKL_D U3 exec(const Point& pt, const ParamsType& p) {
+    const uint8_t* q = p.src + static_cast<int64_t>(p.ry + pt.y) * p.pitch + 3 * (p.rx + pt.x);
+    return U3{{__ldg(q), __ldg(q + 1), __ldg(q + 2)}};
+  }
+};
+
+// Horizontal fusion (paper §IV-B, BatchRead): an array of per-image params
+// indexed by thread.z; `count` disables the unused entries.
+template <class ROp, int CAP>
+struct BatchRead {
+  using InstanceType = ReadType;
+  using OutputType = typename ROp::OutputType;
+  struct ParamsType {
+    int32_t count;
+    int32_t _pad[3];
+    typename ROp::ParamsType p[CAP];
+  };
+
+  static FKL_D OutputType exec(const Point& pt, const ParamsType& bp) {
+    return ROp::exec(pt, bp.p[pt.z]);
+  }
+
+  template <class R, int V, class = void>
+  struct HasSpan : std::false_type {};
+  template <class R, int V>
+  struct HasSpan<R, V, std::void_t<decltype(&R::template exec_span<V>)>> : std::true_type {};
+
+  template <int V>
+  static FKL_D void exec_span(const Point& pt, const ParamsType& bp, OutputType (&out)[V]) {
+    const typename ROp::ParamsType& p = bp.p[pt.z];
+    if constexpr (HasSpan<ROp, V>::value) {
+      ROp::template exec_span<V>(pt, p, out);
+    } else {
+#pragma unroll
+      for (int k = 0; k < V; ++k) out[k] = ROp::exec(Point{pt.x + k, pt.y, pt.z}, p);
+    }
+  }
+};
+
+// ===========================================================================
+// Compute Operations
+// ===========================================================================
+
+// ColorConvert BGR <-> RGB: a register permutation.
+template <class P>
+struct SwapRB {
+  using InstanceType = UnaryType;
+  using InputType = P;
+  using OutputType = P;
+  static FKL_D P exec(const P& x) {
+    P o = x;
+    o.v[0] = x.v[2];
+    o.v[2] = x.v[0];
+    return o;
+  }
+};
+
+struct C3Params {
+  float c[3];
+};
+
+struct Mul3 {
+  using InstanceType = BinaryType;
+  using InputType = F3;
+  using OutputType = F3;
+  using ParamsType = C3Params;
+  static FKL_D F3 exec(const F3& x, const ParamsType& p) {
+    return F3{{__fmul_rn(x.v[0], p.c[0]), __fmul_rn(x.v[1], p.c[1]), __fmul_rn(x.v[2], p.c[2])}};
+  }
+};
+struct Sub3 {
+  using InstanceType = BinaryType;
+  using InputType = F3;
+  using OutputType = F3;
+  using ParamsType = C3Params;
+  static FKL_D F3 exec(const F3& x, const ParamsType& p) {
+    return F3{{__fsub_rn(x.v[0], p.c[0]), __fsub_rn(x.v[1], p.c[1]), __fsub_rn(x.v[2], p.c[2])}};
+  }
+};
+// IEEE division. `on` = 0 passes the value through untouched (a chain
+// without a Divide), which skips the cost of dividing by one.
+struct Div3Params {
+  float c[3];
+  int32_t on;
+};
+struct Div3 {
+  using InstanceType = BinaryType;
+  using InputType = F3;
+  using OutputType = F3;
+  using ParamsType = Div3Params;
+  static FKL_D F3 exec(const F3& x, const ParamsType& p) {
+    if (!p.on) return x;
+    return F3{{__fdiv_rn(x.v[0], p.c[0]), __fdiv_rn(x.v[1], p.c[1]), __fdiv_rn(x.v[2], p.c[2])}};
+  }
+};
+
+struct I3Params {
+  int32_t k[3];
+};
+// Saturating u8 add of an integer per channel: clamp(x + k, 0, 255).
+struct AddSatU8 {
+  using InstanceType = BinaryType;
+  using InputType = U3;
+  using OutputType = U3;
+  using ParamsType = I3Params;
+  static FKL_D U3 exec(const U3& x, const ParamsType& p) {
+    U3 o;
+#pragma unroll
+    for (int c = 0; c < 3; ++c) o.v[c] = static_cast<uint8_t>(min(255, max(0, static_cast<int>(x.v[c]) + p.k[c])));
+    return o;
+  }
+};
+
+// ===========================================================================
+// Write Operations
+// ===========================================================================
+
+// Output tensor of a batch of images: element (z, c, y, x) of a planar
+// tensor lives at base + z*img + c*plane + y*pitch + x*bytes; a packed
+// tensor uses (z, y, x, c) at base + z*img + y*pitch + (x*C + c)*bytes.
+struct OutParams {
+  uint8_t* base;
+  int64_t img;
+  int64_t plane;
+  int64_t pitch;
+  float scale_inv;  // FP8: the stored value is x * scale_inv
+  int32_t aligned;  // 1: every run start is aligned for vector stores
+};
+
+template <class OutT>
+FKL_D float prescale(float x, const OutParams& p) {
+  if constexpr (std::is_same_v<OutT, e4m3_t>) return __fmul_rn(x, p.scale_inv);
+  return x;
+}
+
+// Split (paper Fig. 9): packed pixel -> C planes.
+template <class OutT, int C = 3>
+struct WriteSplit {
+  using InstanceType = WriteType;
+  using InputType = Pix<float, C>;
+  using ParamsType = OutParams;
+  static constexpr int B = Format<OutT>::bytes;
+
+  static FKL_D void exec(const Point& pt, const InputType& v, const ParamsType& p) {
+    uint8_t* q = p.base + pt.z * p.img + pt.y * p.pitch + static_cast<int64_t>(pt.x) * B;
+#pragma unroll
+    for (int c = 0; c < C; ++c) store_one<OutT>(q + c * p.plane, prescale<OutT>(v.v[c], p));
+  }
+
+  // n <= V valid pixels starting at pt.x.
+  template <int V>
+  static FKL_D void exec_span(const Point& pt, int n, const InputType (&v)[V], const ParamsType& p) {
+    uint8_t* q = p.base + pt.z * p.img + pt.y * p.pitch + static_cast<int64_t>(pt.x) * B;
+    if (n == V && p.aligned) {
+#pragma unroll
+      for (int c = 0; c < C; ++c) {
+        float run[V];
+#pragma unroll
+        for (int k = 0; k < V; ++k) run[k] = prescale<OutT>(v[k].v[c], p);
+        store_run<OutT, V>(q + c * p.plane, run);
+      }
+    } else {
+#pragma unroll
+      for (int k = 0; k < V; ++k) {
+        if (k < n) {
+#pragma unroll
+          for (int c = 0; c < C; ++c) store_one<OutT>(q + c * p.plane + k * B, prescale<OutT>(v[k].v[c], p));
+        }
+      }
+    }
+  }
+};
+
+// Packed store: C consecutive values per pixel.
+template <class OutT, int C = 3>
+struct WritePacked {
+  using InstanceType = WriteType;
+  using InputType = Pix<float, C>;
+  using ParamsType = OutParams;
+  static constexpr int B = Format<OutT>::bytes;
+
+  static FKL_D void exec(const Point& pt, const InputType& v, const ParamsType& p) {
+    uint8_t* q = p.base + pt.z * p.img + pt.y * p.pitch + static_cast<int64_t>(pt.x) * C * B;
+#pragma unroll
+    for (int c = 0; c < C; ++c) store_one<OutT>(q + c * B, prescale<OutT>(v.v[c], p));
+  }
+  template <int V>
+  static FKL_D void exec_span(const Point& pt, int n, const InputType (&v)[V], const ParamsType& p) {
+    uint8_t* q = p.base + pt.z * p.img + pt.y * p.pitch + static_cast<int64_t>(pt.x) * C * B;
+    if constexpr ((V * C) % 4 == 0) {
+      if (n == V && p.aligned) {
+        float run[V * C];
+#pragma unroll
+        for (int k = 0; k < V; ++k)
+#pragma unroll
+          for (int c = 0; c < C; ++c) run[k * C + c] = prescale<OutT>(v[k].v[c], p);
+        store_run<OutT, V * C>(q, run);
+        return;
+      }
+    }
+#pragma unroll
+    for (int k = 0; k < V; ++k) {
+      if (k < n) {
+#pragma unroll
+        for (int c = 0; c < C; ++c) store_one<OutT>(q + (k * C + c) * B, prescale<OutT>(v[k].v[c], p));
+      }
+    }
+  }
+};
+
+// u8 outputs of the integer chains.
+template <bool kSplit>
+struct WriteU8C3 {
+  using InstanceType = WriteType;
+  using InputType = U3;
+  using ParamsType = OutParams;
+  static FKL_D void exec(const Point& pt, const U3& v, const ParamsType& p) {
+    uint8_t* q = p.base + pt.z * p.img + pt.y * p.pitch;
+    if constexpr (kSplit) {
+#pragma unroll
+      for (int c = 0; c < 3; ++c) q[c * p.plane + pt.x] = v.v[c];
+    } else {
+#pragma unroll
+      for (int c = 0; c < 3; ++c) q[3 * pt.x + c] = v.v[c];
+    }
+  }
+  template <int V>
+  static FKL_D void exec_span(const Point& pt, int n, const U3 (&v)[V], const ParamsType& p) {
+    uint8_t* q = p.base + pt.z * p.img + pt.y * p.pitch;
+    if constexpr (kSplit && V % 4 == 0) {
+      if (n == V && p.aligned) {
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+          uint32_t w[V / 4];
+#pragma unroll
+          for (int i = 0; i < V / 4; ++i)
+            w[i] = v[4 * i].v[c] | (v[4 * i + 1].v[c] << 8) | (v[4 * i + 2].v[c] << 16) |
+                   (static_cast<uint32_t>(v[4 * i + 3].v[c]) << 24);
+          store_words<V / 4>(q + c * p.plane + pt.x, w);
+        }
+        return;
+      }
+    }
+#pragma unroll
+    for (int k = 0; k < V; ++k)
+      if (k < n) exec(Point{pt.x + k, pt.y, pt.z}, v[k], p);
+  }
+};
+
+}  // namespace fkl

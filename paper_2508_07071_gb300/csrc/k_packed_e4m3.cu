@@ -1,0 +1,9 @@
+// Compiled float chains over packed 3-channel u8 images (crop, bilinear resize, placement),
+// writing e4m3 outputs.
+#include "float_family.cuh"
+
+namespace fkl_impl {
+
+cudaError_t launch_packed_e4m3(const LaunchCtx& c) { return float_dispatch_type<fkl::ResizeU8C3, fkl::e4m3_t>(c); }
+
+}  // namespace fkl_impl

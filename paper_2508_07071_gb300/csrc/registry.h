@@ -1,0 +1,82 @@
+// Internal interface between the C ABI (api.cu) and the translation units
+// that hold the compiled chain instantiations (k_*.cu).
+#pragma once
+
+#include <cstdint>
+#include <vector>
+
+#include "../../include/fkl.h"
+#include "fkl/dpp.cuh"
+
+namespace fkl_impl {
+
+enum Family { FAM_PACKED = 1, FAM_NV12 = 2, FAM_INT = 3, FAM_VCHAIN = 4 };
+enum Geom { GEOM_NONE = 0, GEOM_RESIZE = 1, GEOM_LETTERBOX = 2 };
+
+// A parsed chain: which compiled family runs it and the runtime parameters
+// of every op (absent arithmetic ops hold their identity constants).
+struct Spec {
+  Family family;
+  bool has_crop = false;
+  int32_t crop[4] = {0, 0, 0, 0};
+  Geom geom = GEOM_NONE;
+  int32_t out_w = 0, out_h = 0;
+  float pad = 0.f;
+  bool swap = false;
+  bool has_mul = false, has_sub = false, has_div = false, has_addsat = false;
+  float mul[3] = {1.f, 1.f, 1.f};
+  float sub[3] = {0.f, 0.f, 0.f};  // ADD c is stored as SUB -c (same bits)
+  float div[3] = {1.f, 1.f, 1.f};
+  int32_t addsat[3] = {0, 0, 0};
+  bool split = true;
+  int32_t out_dtype = FKL_F32;
+  float fp8_scale = 1.f;
+  std::vector<int32_t> vkinds;  // vertical chain: 0 = Mul, 1 = Add
+  std::vector<float> vconsts;
+};
+
+// One launch of an image family: up to kBatchCap images.
+constexpr int kBatchCap = 256;
+
+struct LaunchCtx {
+  const Spec* spec;
+  fkl_launch_shape shape;
+  const fkl::ResampleParams* imgs;  // host array of n entries
+  int n;
+  fkl::OutParams out;
+  int H, W;
+  cudaStream_t stream;
+};
+
+// Fused launches of the float image families, one translation unit per
+// (source, output type): k_<src>_<type>.cu.
+cudaError_t launch_packed_f32(const LaunchCtx& c);
+cudaError_t launch_packed_f16(const LaunchCtx& c);
+cudaError_t launch_packed_bf16(const LaunchCtx& c);
+cudaError_t launch_packed_e4m3(const LaunchCtx& c);
+cudaError_t launch_nv12_f32(const LaunchCtx& c);
+cudaError_t launch_nv12_f16(const LaunchCtx& c);
+cudaError_t launch_nv12_bf16(const LaunchCtx& c);
+cudaError_t launch_nv12_e4m3(const LaunchCtx& c);
+// Integer chains (k_int.cu).
+cudaError_t launch_int(const LaunchCtx& c);
+// Vertical chain (k_vchain.cu): one fused launch per chunk of ops.
+constexpr int kVChainCap = 4096;
+cudaError_t launch_vchain(const Spec& s, const float* in, float* out, int64_t n,
+                          cudaStream_t stream);
+
+// Unfused reference form (k_unfused.cu): one kernel per op for one image;
+// ws0 and ws1 each hold one intermediate image.
+cudaError_t launch_unfused_image(const Spec& s, const fkl::ResampleParams& img,
+                                 const fkl::OutParams& out, int z, int H, int W,
+                                 void* ws0, void* ws1, cudaStream_t stream);
+cudaError_t launch_unfused_vchain(const Spec& s, const float* in, float* out, int64_t n,
+                                  cudaStream_t stream);
+
+// Launch shapes compiled for a family/dtype (the autotuner's search space).
+std::vector<fkl_launch_shape> shapes_for(const Spec& s);
+fkl_launch_shape default_shape(const Spec& s);
+
+int sm_count();
+
+}  // namespace fkl_impl

@@ -1,0 +1,374 @@
+"""Parity of the CUDA path (through the C ABI) with the CPU oracle.
+
+Small cases are compared element by element; the full-size workloads run in
+the launch configuration the benchmark times and are compared on sampled
+images (or sampled elements for the elementwise vertical chain).
+"""
+import numpy as np
+import pytest
+
+import oracle as O
+from paper_2508_07071_gb300 import synth
+from parity import check_f32, check_output, check_lowp, to_numpy
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+@pytest.fixture(scope="module")
+def F():
+    if not torch.cuda.is_available():
+        pytest.skip("needs a GPU")
+    from paper_2508_07071_gb300 import build
+    build.build()
+    from paper_2508_07071_gb300 import fkl
+    return fkl
+
+
+@pytest.fixture(scope="module")
+def W():
+    from paper_2508_07071_gb300 import workloads
+    return workloads
+
+
+def code(F, fmt):
+    return {"f32": F.FKL_F32, "f16": F.FKL_F16, "bf16": F.FKL_BF16, "e4m3": F.FKL_E4M3, "u8": F.FKL_U8}[fmt]
+
+
+def tdtype(fmt):
+    return {"f32": torch.float32, "f16": torch.float16, "bf16": torch.bfloat16,
+            "e4m3": torch.float8_e4m3fn, "u8": torch.uint8}[fmt]
+
+
+def run_batch(F, ops, srcs, rois, out_shape, fmt, layout_in=None, unfused=False, shape=None):
+    p = F.Pipeline(ops)
+    if shape is not None:
+        F.fkl_pipeline_set_shape(p.handle, shape)
+    out = torch.full(out_shape, float("nan") if fmt != "u8" and fmt != "e4m3" else 0,
+                     dtype=tdtype(fmt), device="cuda")
+    layout = F.FKL_LAYOUT_NCHW if out_shape[1] == 3 else F.FKL_LAYOUT_NHWC
+    ins = [F.as_fkl(s, layout_in) for s in srcs]
+    o = F.as_fkl(out, layout)
+    if unfused:
+        nbytes = F.fkl_unfused_workspace_bytes(p.handle, ins, rois, o)
+        ws = torch.empty(max(nbytes, 256), dtype=torch.uint8, device="cuda")
+        F.fkl_execute_batch_unfused(p.handle, ins, rois, o, ws.data_ptr(), nbytes)
+    else:
+        F.fkl_execute_batch(p.handle, ins, rois, o)
+    torch.cuda.synchronize()
+    return out
+
+
+# ------------------------------------------------------------------ single image (crop -> resize -> normalise)
+
+
+def test_single_image_full_size(F, W):
+    cfg = W.SINGLE
+    src = synth.packed_image(0, cfg["src_h"], cfg["src_w"])
+    ops = W.normalize_chain(cfg["out_w"], cfg["out_h"], roi=cfg["roi"])
+    out = run_batch(F, ops, [torch.from_numpy(src).cuda()], None, (1, 3, cfg["out_h"], cfg["out_w"]), "f32")
+    want = O.preprocess_packed(src, cfg["roi"], cfg["out_w"], cfg["out_h"], swap=True, mul=1 / 255,
+                               sub=W.IMAGENET_MEAN, div=W.IMAGENET_STD)
+    check_f32(to_numpy(out)[0], want, "single image")
+
+
+def test_hf_batch_full_size(F, W):
+    cfg = W.HF
+    frame = synth.packed_image(1, cfg["src_h"], cfg["src_w"])
+    rois = synth.crop_rois(1, cfg["n"], cfg["src_w"], cfg["src_h"], cfg["w_range"], cfg["h_range"])
+    dframe = torch.from_numpy(frame).cuda()
+    ops = W.normalize_chain(cfg["out_w"], cfg["out_h"])
+    out = run_batch(F, ops, [dframe] * cfg["n"], rois, (cfg["n"], 3, cfg["out_h"], cfg["out_w"]), "f32")
+    want = O.preprocess_packed_batch([frame] * cfg["n"], rois, cfg["out_w"], cfg["out_h"], swap=True,
+                                     mul=1 / 255, sub=W.IMAGENET_MEAN, div=W.IMAGENET_STD)
+    check_f32(to_numpy(out), want, "HF batch")
+
+
+@pytest.mark.parametrize("fmt", ["f32", "f16", "bf16", "e4m3"])
+@pytest.mark.parametrize("swap", [True, False])
+def test_packed_formats(F, W, fmt, swap):
+    src = synth.packed_image(2, 90, 131)
+    rois = np.array([[0, 0, 131, 90], [5, 7, 60, 41], [100, 50, 31, 40]], np.int32)
+    scale = W.E4M3_SCALE if fmt == "e4m3" else None
+    mean, std = W.IMAGENET_MEAN, W.IMAGENET_STD
+    ops = [F.read_u8c3(), F.resize(37, 23)] + ([F.swap_rb()] if swap else []) + [
+        F.mul(W.INV255), F.sub(mean), F.div(std), F.write_split(code(F, fmt), scale)]
+    d = torch.from_numpy(src).cuda()
+    out = run_batch(F, ops, [d] * 3, rois, (3, 3, 23, 37), fmt)
+    want = O.preprocess_packed_batch([src] * 3, rois, 37, 23, swap=swap, mul=1 / 255, sub=mean, div=std)
+    if fmt == "e4m3":
+        # normalised values exceed [0, 1]; |v| / scale stays finite and saturates at 448
+        check_output(out, want, fmt, scale, "packed e4m3")
+    else:
+        check_output(out, want, fmt, 1.0, f"packed {fmt}")
+
+
+@pytest.mark.parametrize("src_hw,roi,out_wh", [
+    ((7, 5), (0, 0, 5, 7), (19, 13)),          # upscale with border clamp
+    ((1, 1), (0, 0, 1, 1), (9, 4)),            # 1x1 source
+    ((50, 60), (59, 49, 1, 1), (3, 3)),        # corner pixel
+    ((33, 47), (3, 2, 40, 30), (40, 30)),      # identity resize = exact copy
+    ((480, 640), (1, 1, 637, 477), (224, 224)),
+    ((64, 33), (0, 0, 33, 64), (128, 64)),     # ragged width
+])
+def test_packed_geometry_edges(F, W, src_hw, roi, out_wh):
+    src = synth.packed_image(3, *src_hw)
+    ops = [F.read_u8c3(), F.crop(*roi), F.resize(*out_wh), F.write_split(F.FKL_F32)]
+    out = run_batch(F, ops, [torch.from_numpy(src).cuda()], None, (1, 3, out_wh[1], out_wh[0]), "f32")
+    want = O.preprocess_packed(src, roi, out_wh[0], out_wh[1], swap=False)
+    check_f32(to_numpy(out)[0], want, f"geometry {src_hw} {roi} {out_wh}")
+    if roi[2:] == out_wh:  # identity resize reproduces the crop exactly
+        assert np.array_equal(to_numpy(out)[0], O.split(O.crop(src, *roi).astype(np.float64)))
+
+
+def test_crop_only_float_chain(F):
+    src = synth.packed_image(4, 20, 30)
+    ops = [F.read_u8c3(), F.crop(2, 3, 17, 11), F.mul(0.5), F.write_split(F.FKL_F32)]
+    out = run_batch(F, ops, [torch.from_numpy(src).cuda()], None, (1, 3, 11, 17), "f32")
+    want = O.split(O.multiply(O.to_float(O.crop(src, 2, 3, 17, 11)), 0.5))
+    assert np.array_equal(to_numpy(out)[0], want)
+
+
+def test_packed_output_layout(F, W):
+    src = synth.packed_image(5, 40, 60)
+    ops = [F.read_u8c3(), F.resize(21, 13), F.swap_rb(), F.mul(W.INV255), F.write_packed(F.FKL_F32)]
+    out = run_batch(F, ops, [torch.from_numpy(src).cuda()], None, (1, 13, 21, 3), "f32")
+    want = O.preprocess_packed(src, (0, 0, 60, 40), 21, 13, swap=True, mul=1 / 255)
+    check_f32(to_numpy(out)[0], np.moveaxis(want, 0, -1), "packed output")
+
+
+def test_large_batch_multi_launch(F, W):
+    src = synth.packed_image(6, 64, 64)
+    rois = synth.crop_rois(6, 300, 64, 64, (4, 40), (4, 40))
+    ops = W.normalize_chain(16, 8)
+    d = torch.from_numpy(src).cuda()
+    out = run_batch(F, ops, [d] * 300, rois, (300, 3, 8, 16), "f32")
+    want = O.preprocess_packed_batch([src] * 300, rois, 16, 8, swap=True, mul=1 / 255,
+                                     sub=W.IMAGENET_MEAN, div=W.IMAGENET_STD)
+    check_f32(to_numpy(out), want, "300 images")
+
+
+def test_empty_batch_is_a_no_op(F, W):
+    p = F.Pipeline(W.normalize_chain(16, 8))
+    out = torch.zeros((1, 3, 8, 16), device="cuda")
+    F.fkl_execute_batch(p.handle, [], None, F.as_fkl(out, F.FKL_LAYOUT_NCHW))
+    torch.cuda.synchronize()
+    assert float(out.abs().sum()) == 0.0
+
+
+def test_unaligned_pitches_take_scalar_paths(F, W):
+    src = synth.packed_image(7, 40, 50)
+    big = torch.zeros((40, 51, 3), dtype=torch.uint8)
+    big[:, :50] = torch.from_numpy(src)
+    d = big.cuda()[:, :50]                      # row pitch 153 bytes
+    outbuf = torch.full((1, 3, 20, 27), float("nan"), device="cuda")
+    out = outbuf[..., :25]                      # output pitch 108 bytes
+    p = F.Pipeline(W.normalize_chain(25, 20))
+    F.fkl_execute(p.handle, F.as_fkl(d), F.as_fkl(out, F.FKL_LAYOUT_NCHW))
+    torch.cuda.synchronize()
+    want = O.preprocess_packed(src, (0, 0, 50, 40), 25, 20, swap=True, mul=1 / 255,
+                               sub=W.IMAGENET_MEAN, div=W.IMAGENET_STD)
+    check_f32(to_numpy(out)[0], want, "unaligned")
+    assert torch.isnan(outbuf[..., 25:]).all()  # nothing written past the row
+
+
+# ------------------------------------------------------------------ NV12 -> letterbox
+
+
+def nv12_case(F, W, fmt, frames, out=640, shape=None, unfused=False, rois=None):
+    dev = torch.from_numpy(frames).cuda()
+    ops = W.nv12_letterbox_chain(code(F, fmt), out=out)
+    scale = W.E4M3_SCALE if fmt == "e4m3" else 1.0
+    res = run_batch(F, ops, [dev[i] for i in range(len(frames))], rois, (len(frames), 3, out, out), fmt,
+                    layout_in=F.FKL_LAYOUT_NV12, unfused=unfused, shape=shape)
+    return res, scale
+
+
+@pytest.mark.parametrize("fmt", ["bf16", "f16", "e4m3", "f32"])
+def test_nv12_letterbox_small_batch(F, W, fmt):
+    frames = synth.nv12_frames(3, 3, 720, 1280)
+    out, scale = nv12_case(F, W, fmt, frames)
+    for i in range(len(frames)):
+        want = O.preprocess_nv12(frames[i], 640, 640, pad=114.0, mul=1 / 255)
+        stats = check_output(out[i], want, fmt, scale, f"nv12 {fmt} frame {i}")
+        if fmt != "f32":
+            # one ulp of the format at the top of the [0, 1] range
+            assert stats["max_abs_err_vs_fp64"] <= {"bf16": 2 ** -8, "f16": 2 ** -11, "e4m3": 32 * scale}[fmt]
+
+
+def test_nv12_full_batch_sampled(F, W):
+    cfg = W.NV12
+    frames = synth.nv12_frames(3, cfg["n"], cfg["h"], cfg["w"])
+    out, _ = nv12_case(F, W, "bf16", frames)
+    for i in [0, 1, 77, 128, 200, cfg["n"] - 1]:
+        want = O.preprocess_nv12(frames[i], 640, 640, pad=114.0, mul=1 / 255)
+        check_output(out[i], want, "bf16", 1.0, f"full batch frame {i}")
+
+
+@pytest.mark.parametrize("hw,out,roi", [
+    ((720, 1280), 512, None),                  # 2.5x: general bilinear path
+    ((480, 640), 640, None),                   # upscale
+    ((96, 130), 64, [(3, 5, 101, 77)]),        # odd crop offsets and sizes
+    ((64, 48), 32, [(16, 8, 32, 40)]),         # 2x with 16-aligned crop: vector path
+])
+def test_nv12_general_geometry(F, W, hw, out, roi):
+    frames = synth.nv12_frames(4, 1, *hw)
+    dev = torch.from_numpy(frames).cuda()
+    ops = [F.read_nv12(), F.letterbox(out, out, 114.0), F.mul(W.INV255), F.write_split(F.FKL_F32)]
+    res = run_batch(F, ops, [dev[0]], roi, (1, 3, out, out), "f32", layout_in=F.FKL_LAYOUT_NV12)
+    rgb = O.nv12_to_rgb(frames[0])
+    if roi is not None:
+        x, y, w, h = roi[0]
+        rgb = rgb[y:y + h, x:x + w]
+    want = O.split(O.multiply(O.letterbox(rgb, out, out, 114.0), 1 / 255))
+    check_f32(to_numpy(res)[0], want, f"nv12 geometry {hw} {out} {roi}")
+
+
+def test_nv12_resize_with_normalise(F, W):
+    frames = synth.nv12_frames(5, 2, 360, 640)
+    dev = torch.from_numpy(frames).cuda()
+    ops = [F.read_nv12(), F.resize(320, 180), F.swap_rb(), F.mul(W.INV255), F.sub(W.IMAGENET_MEAN),
+           F.div(W.IMAGENET_STD), F.write_split(F.FKL_F16)]
+    res = run_batch(F, ops, [dev[0], dev[1]], None, (2, 3, 180, 320), "f16", layout_in=F.FKL_LAYOUT_NV12)
+    for i in range(2):
+        rgb = O.nv12_to_rgb(frames[i])
+        t = O.swap_rb(O.resize_bilinear(rgb, 320, 180))
+        want = O.split(O.divide(O.subtract(O.multiply(t, 1 / 255), W.IMAGENET_MEAN), W.IMAGENET_STD))
+        check_output(res[i], want, "f16", 1.0, "nv12 normalise")
+
+
+# ------------------------------------------------------------------ vertical chain
+
+
+@pytest.mark.parametrize("L", [0, 1, 2, 10, 100, 1000, 4099])
+def test_vertical_chain_bit_exact(F, W, L):
+    n = 100_003
+    x = synth.f32_uniform(2, n)
+    kinds, consts = synth.chain_constants(2, L)
+    p = F.Pipeline(W.vertical_chain(kinds, consts))
+    xin = torch.from_numpy(x).cuda()
+    out = torch.empty_like(xin)
+    F.fkl_execute(p.handle, F.as_fkl(xin), F.as_fkl(out))
+    torch.cuda.synchronize()
+    want = O.vertical_chain_f32(x, kinds, consts)
+    assert np.array_equal(out.cpu().numpy().view(np.uint32), want.view(np.uint32))
+
+
+def test_vertical_chain_irregular_kinds_in_place(F, W):
+    rng = np.random.default_rng(9)
+    kinds = rng.integers(0, 2, 333)
+    consts = rng.uniform(0.5, 1.5, 333).astype(np.float32)
+    x = synth.f32_uniform(3, 4097)
+    buf = torch.from_numpy(x).cuda()
+    p = F.Pipeline(W.vertical_chain(kinds, consts))
+    F.fkl_execute(p.handle, F.as_fkl(buf), F.as_fkl(buf))
+    torch.cuda.synchronize()
+    want = O.vertical_chain_f32(x, kinds, consts)
+    assert np.array_equal(buf.cpu().numpy().view(np.uint32), want.view(np.uint32))
+
+
+@pytest.mark.parametrize("L", [1, 10, 1000])
+def test_vertical_chain_full_size_sampled(F, W, L):
+    n = W.VCHAIN["n"]
+    x = synth.f32_uniform(2, n)
+    kinds, consts = synth.chain_constants(2, L)
+    p = F.Pipeline(W.vertical_chain(kinds, consts))
+    xin = torch.from_numpy(x).cuda()
+    out = torch.empty_like(xin)
+    F.fkl_execute(p.handle, F.as_fkl(xin), F.as_fkl(out))
+    torch.cuda.synchronize()
+    idx = np.unique(np.concatenate([np.random.default_rng(L).integers(0, n, 20000), [0, n - 1]]))
+    want = O.vertical_chain_f32(x[idx], kinds, consts)
+    got = out[torch.from_numpy(idx).cuda()].cpu().numpy()
+    assert np.array_equal(got.view(np.uint32), want.view(np.uint32))
+
+
+# ------------------------------------------------------------------ integer chains
+
+
+@pytest.mark.parametrize("split", [False, True])
+@pytest.mark.parametrize("swap", [False, True])
+def test_integer_chain_bit_exact(F, W, split, swap):
+    src = synth.packed_image(8, 37, 45)
+    roi = (3, 4, 33, 29)
+    k = (40, -70, 200)
+    ops = W.integer_chain(roi=roi, swap=swap, add_k=k, split=split)
+    shape = (1, 3, 29, 33) if split else (1, 29, 33, 3)
+    out = run_batch(F, ops, [torch.from_numpy(src).cuda()], None, shape, "u8")
+    want = O.integer_chain_packed(src, roi, swap=swap, add_k=k)
+    got = out.cpu().numpy()[0]
+    assert np.array_equal(np.moveaxis(got, 0, -1) if split else got, want)
+
+
+# ------------------------------------------------------------------ unfused form, launch shapes, graphs
+
+
+def test_unfused_equals_fused_bitwise(F, W):
+    cfg = W.HF
+    frame = synth.packed_image(1, 720, 1280)
+    rois = synth.crop_rois(1, 7, 1280, 720, cfg["w_range"], cfg["h_range"])
+    d = torch.from_numpy(frame).cuda()
+    ops = W.normalize_chain(128, 64)
+    a = run_batch(F, ops, [d] * 7, rois, (7, 3, 64, 128), "f32")
+    b = run_batch(F, ops, [d] * 7, rois, (7, 3, 64, 128), "f32", unfused=True)
+    assert torch.equal(a.view(torch.int32), b.view(torch.int32))
+
+    frames = synth.nv12_frames(3, 2, 720, 1280)
+    for fmt in ["bf16", "e4m3"]:
+        a, _ = nv12_case(F, W, fmt, frames)
+        b, _ = nv12_case(F, W, fmt, frames, unfused=True)
+        assert torch.equal(a.view(torch.uint8), b.view(torch.uint8)), fmt
+
+    src = synth.packed_image(8, 37, 45)
+    ops = W.integer_chain(roi=(3, 4, 33, 29), swap=True, add_k=(1, -2, 3), split=True)
+    a = run_batch(F, ops, [torch.from_numpy(src).cuda()], None, (1, 3, 29, 33), "u8")
+    b = run_batch(F, ops, [torch.from_numpy(src).cuda()], None, (1, 3, 29, 33), "u8", unfused=True)
+    assert torch.equal(a, b)
+
+    kinds, consts = synth.chain_constants(2, 37)
+    x = torch.from_numpy(synth.f32_uniform(2, 5000)).cuda()
+    p = F.Pipeline(W.vertical_chain(kinds, consts))
+    y1, y2 = torch.empty_like(x), torch.empty_like(x)
+    F.fkl_execute(p.handle, F.as_fkl(x), F.as_fkl(y1))
+    F.fkl_execute_batch_unfused(p.handle, [F.as_fkl(x)], None, F.as_fkl(y2), 0, 0)
+    torch.cuda.synchronize()
+    assert torch.equal(y1.view(torch.int32), y2.view(torch.int32))
+
+
+def test_every_launch_shape_gives_the_same_bytes(F, W):
+    frames = synth.nv12_frames(3, 2, 720, 1280)
+    base, _ = nv12_case(F, W, "bf16", frames)
+    p = F.Pipeline(W.nv12_letterbox_chain(F.FKL_BF16))
+    for shape in F.fkl_pipeline_shapes(p.handle):
+        got, _ = nv12_case(F, W, "bf16", frames, shape=shape)
+        assert torch.equal(got.view(torch.uint8), base.view(torch.uint8)), shape
+
+    src = synth.packed_image(2, 90, 131)
+    rois = np.array([[0, 0, 131, 90], [5, 7, 60, 41]], np.int32)
+    ops = W.normalize_chain(37, 23)
+    d = torch.from_numpy(src).cuda()
+    base = run_batch(F, ops, [d, d], rois, (2, 3, 23, 37), "f32")
+    p = F.Pipeline(ops)
+    for shape in F.fkl_pipeline_shapes(p.handle):
+        got = run_batch(F, ops, [d, d], rois, (2, 3, 23, 37), "f32", shape=shape)
+        assert torch.equal(got.view(torch.int32), base.view(torch.int32)), shape
+
+
+def test_cuda_graph_capture_replays(F, W):
+    frames = synth.nv12_frames(3, 4, 720, 1280)
+    dev = torch.from_numpy(frames).cuda()
+    p = F.Pipeline(W.nv12_letterbox_chain(F.FKL_BF16))
+    out = torch.zeros((4, 3, 640, 640), dtype=torch.bfloat16, device="cuda")
+    ins = [F.as_fkl(dev[i], F.FKL_LAYOUT_NV12) for i in range(4)]
+    o = F.as_fkl(out, F.FKL_LAYOUT_NCHW)
+    s = torch.cuda.Stream()
+    with torch.cuda.stream(s):
+        F.fkl_execute_batch(p.handle, ins, None, o, stream=s)  # warm up outside the capture
+    torch.cuda.synchronize()
+    ref = out.clone()
+    out.zero_()
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g, stream=s):
+        F.fkl_execute_batch(p.handle, ins, None, o, stream=s)
+    g.replay()
+    torch.cuda.synchronize()
+    assert torch.equal(out.view(torch.uint8), ref.view(torch.uint8))
