@@ -271,7 +271,17 @@ def run_ours(args):
     wl = make_workload(args, F, W, synth, metrics, torch)
     stream = torch.cuda.Stream()
     between = getattr(wl, "between_steps", None)
+    tuned = None
     with torch.cuda.stream(stream):
+        if args.shape:
+            F.fkl_pipeline_set_shape(wl.pipe.handle, [int(v) for v in args.shape.split(",")])
+        elif not args.no_autotune:
+            ins = wl.ins if hasattr(wl, "ins") else [wl.i]
+            rois = getattr(wl, "rois", None)
+            best, us = F.fkl_pipeline_autotune(wl.pipe.handle, ins, rois, wl.o, stream=stream,
+                                               reps=args.autotune_reps)
+            tuned = {"shape": list(best), "us_per_launch": round(us, 2),
+                     "candidates": len(F.fkl_pipeline_shapes(wl.pipe.handle))}
         for _ in range(args.warmup):
             wl.step(stream)
         torch.cuda.synchronize()
@@ -334,7 +344,7 @@ def run_ours(args):
                                  else "L2 flushed (256 MiB write) between timed steps, outside the events"),
                    "parallelism": f"replicas x{world}", "launch_shape": list(F.fkl_pipeline_get_shape(wl.pipe.handle))
                    if hasattr(wl, "pipe") else None,
-                   "kernel": F.fkl_pipeline_kernel_name(wl.pipe.handle)},
+                   "kernel": F.fkl_pipeline_kernel_name(wl.pipe.handle), "autotune": tuned},
         "unfused": None if unfused_ms is None else {
             "ms_per_step": round(unfused_ms, 4), "speedup": round(unfused_ms / ms_per_step, 2),
             "traffic_ratio": round(wl.unfused_bytes() / wl.bytes, 2), "steps": ku,
@@ -432,6 +442,9 @@ def main():
     ap.add_argument("--e2e-steps", type=int, default=10)
     ap.add_argument("--cpu-seconds", type=float, default=10.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-autotune", action="store_true")
+    ap.add_argument("--autotune-reps", type=int, default=3)
+    ap.add_argument("--shape", default="", help="vec,tx,ty,ry launch shape (skips the autotuner)")
     args = ap.parse_args()
     if args.warmup < 3:
         raise SystemExit("--warmup must be >= 3")

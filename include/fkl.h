@@ -217,12 +217,17 @@ FKL_API fkl_status fkl_execute_batch_unfused(fkl_pipeline p, int32_t n,
  * by the pipeline and valid until fkl_pipeline_destroy. */
 FKL_API const char* fkl_pipeline_kernel_name(fkl_pipeline p);
 
-/* Launch shape used by the fused kernel: V output pixels (elements) per
- * thread, a TX x TY thread block, RY rows per thread. */
+/* Launch shape used by the fused kernel.
+ * Image chains: V output pixels per thread along x, a TX x TY thread block
+ * (TX * TY <= 256), RY output rows per thread.
+ * Float32 tensor chains: `vec` elements per thread and iteration (8, 16 or
+ * 32), TX threads per block (TY = 1); RY = 1 runs a persistent grid of
+ * (2048 / TX) blocks per SM striding over the tensor, RY = 0 one block per
+ * TX * vec elements. */
 typedef struct {
-  int32_t vec;      /* pixels per thread along x: 4, 8 or 16              */
-  int32_t tx, ty;   /* threads per block along x and y (tx*ty <= 1024)   */
-  int32_t ry;       /* output rows per thread: 1 or 2                     */
+  int32_t vec;      /* pixels (elements) per thread along x               */
+  int32_t tx, ty;   /* threads per block along x and y                    */
+  int32_t ry;       /* output rows per thread (image chains)              */
 } fkl_launch_shape;
 
 /* Current / set the launch shape. fkl_pipeline_set_shape validates it
@@ -235,6 +240,19 @@ FKL_API fkl_status fkl_pipeline_set_shape(fkl_pipeline p, const fkl_launch_shape
 FKL_API int32_t fkl_pipeline_shape_count(fkl_pipeline p);
 FKL_API fkl_status fkl_pipeline_shape_at(fkl_pipeline p, int32_t k,
                                  fkl_launch_shape* shape);
+
+/*
+ * Autotuner (tile, coarsening and block shape): runs every launch shape
+ * fkl_pipeline_shape_at lists on these arguments -- one warm-up launch, then
+ * `reps` launches timed with CUDA events on `stream` -- and keeps the fastest
+ * as the pipeline's shape. `best` and `best_us` (mean microseconds per launch,
+ * may be NULL) report it. Every trial writes `out`. Synchronises `stream`;
+ * not capturable in a CUDA graph. A pipeline with a single shape returns it
+ * without timing.
+ */
+FKL_API fkl_status fkl_pipeline_autotune(fkl_pipeline p, int32_t n, const fkl_tensor* ins,
+                                         const int32_t* rois, fkl_tensor* out, void* stream,
+                                         int32_t reps, fkl_launch_shape* best, float* best_us);
 
 /* Library version string. */
 FKL_API const char* fkl_version(void);

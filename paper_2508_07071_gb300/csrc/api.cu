@@ -335,7 +335,11 @@ std::vector<fkl_launch_shape> shapes_for(const Spec& s) {
     else
       vecs = {8, 16};
   } else {
-    return {};
+    std::vector<fkl_launch_shape> out;
+    for (int v : {8, 16, 32})
+      for (int tx : {128, 256, 512})
+        for (int ry : {1, 0}) out.push_back(fkl_launch_shape{v, tx, 1, ry});
+    return out;
   }
   std::vector<fkl_launch_shape> out;
   for (int v : vecs)
@@ -502,8 +506,8 @@ fkl_status fkl_execute(fkl_pipeline p, const fkl_tensor* in, fkl_tensor* out, vo
     const fkl_status st = check_linear(in, out, n);
     if (st != FKL_OK) return st;
     if (n == 0) return FKL_OK;
-    const cudaError_t e = launch_vchain(p->spec, static_cast<const float*>(in->data), static_cast<float*>(out->data),
-                                        n, static_cast<cudaStream_t>(stream));
+    const cudaError_t e = launch_vchain(p->spec, p->shape, static_cast<const float*>(in->data),
+                                        static_cast<float*>(out->data), n, static_cast<cudaStream_t>(stream));
     return e == cudaSuccess ? FKL_OK : cuda_fail(e, "vertical chain launch");
   }
   return fkl_execute_batch(p, 1, in, nullptr, out, stream);
@@ -587,6 +591,59 @@ fkl_status fkl_pipeline_shape_at(fkl_pipeline p, int32_t k, fkl_launch_shape* sh
   const auto v = shapes_for(p->spec);
   if (k < 0 || k >= static_cast<int32_t>(v.size())) return fail(FKL_ERR_INVALID, "shape index %d out of range", k);
   *shape = v[k];
+  return FKL_OK;
+}
+
+fkl_status fkl_pipeline_autotune(fkl_pipeline p, int32_t n, const fkl_tensor* ins, const int32_t* rois,
+                                 fkl_tensor* out, void* stream, int32_t reps, fkl_launch_shape* best,
+                                 float* best_us) {
+  if (!p) return fail(FKL_ERR_INVALID, "null pipeline");
+  if (reps < 1) return fail(FKL_ERR_INVALID, "reps must be >= 1");
+  const bool vchain = p->spec.family == FAM_VCHAIN;
+  auto run = [&]() -> fkl_status {
+    return vchain ? fkl_execute(p, ins, out, stream) : fkl_execute_batch(p, n, ins, rois, out, stream);
+  };
+  const std::vector<fkl_launch_shape> shapes = shapes_for(p->spec);
+  const fkl_launch_shape saved = p->shape;
+  float best_t = -1.f;
+  fkl_launch_shape best_s = saved;
+  if (shapes.size() > 1) {
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    cudaError_t ce = cudaEventCreate(&e0);
+    if (ce == cudaSuccess) ce = cudaEventCreate(&e1);
+    if (ce != cudaSuccess) {
+      if (e0) cudaEventDestroy(e0);
+      return cuda_fail(ce, "autotune event");
+    }
+    fkl_status st = FKL_OK;
+    for (const auto& sh : shapes) {
+      p->shape = sh;
+      st = run();
+      if (st != FKL_OK) break;
+      if ((ce = cudaEventRecord(e0, s)) != cudaSuccess) break;
+      for (int r = 0; r < reps && st == FKL_OK; ++r) st = run();
+      if (st != FKL_OK) break;
+      if ((ce = cudaEventRecord(e1, s)) != cudaSuccess) break;
+      if ((ce = cudaEventSynchronize(e1)) != cudaSuccess) break;
+      float ms = 0.f;
+      if ((ce = cudaEventElapsedTime(&ms, e0, e1)) != cudaSuccess) break;
+      const float us = ms * 1000.f / reps;
+      if (best_t < 0.f || us < best_t) {
+        best_t = us;
+        best_s = sh;
+      }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (st != FKL_OK || ce != cudaSuccess) {
+      p->shape = saved;
+      return st != FKL_OK ? st : cuda_fail(ce, "autotune timing");
+    }
+  }
+  p->shape = best_s;
+  if (best) *best = best_s;
+  if (best_us) *best_us = best_t;
   return FKL_OK;
 }
 

@@ -96,7 +96,7 @@ struct VChainParams {
 };
 
 template <int U, int CAP, bool kAlt>
-__global__ void __launch_bounds__(256) vchain_kernel(const __grid_constant__ VChainParams<CAP> p) {
+__global__ void __launch_bounds__(512) vchain_kernel(const __grid_constant__ VChainParams<CAP> p) {
   constexpr int E = 4 * U;  // elements per thread
   const int64_t stride = static_cast<int64_t>(gridDim.x) * blockDim.x * E;
   for (int64_t base = (static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x) * E; base < p.n;

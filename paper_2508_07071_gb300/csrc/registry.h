@@ -62,8 +62,8 @@ cudaError_t launch_nv12_e4m3(const LaunchCtx& c);
 cudaError_t launch_int(const LaunchCtx& c);
 // Vertical chain (k_vchain.cu): one fused launch per chunk of ops.
 constexpr int kVChainCap = 4096;
-cudaError_t launch_vchain(const Spec& s, const float* in, float* out, int64_t n,
-                          cudaStream_t stream);
+cudaError_t launch_vchain(const Spec& s, const fkl_launch_shape& shape, const float* in, float* out,
+                          int64_t n, cudaStream_t stream);
 
 // Unfused reference form (k_unfused.cu): one kernel per op for one image;
 // ws0 and ws1 each hold one intermediate image.

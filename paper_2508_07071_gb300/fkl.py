@@ -91,6 +91,11 @@ EXPORTS = {
     "fkl_pipeline_shape_count": (ctypes.c_int32, [ctypes.c_void_p]),
     "fkl_pipeline_shape_at": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int32,
                                              ctypes.POINTER(fkl_launch_shape)]),
+    "fkl_pipeline_autotune": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int32, ctypes.POINTER(fkl_tensor),
+                                             ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(fkl_tensor),
+                                             ctypes.c_void_p, ctypes.c_int32,
+                                             ctypes.POINTER(fkl_launch_shape),
+                                             ctypes.POINTER(ctypes.c_float)]),
     "fkl_version": (ctypes.c_char_p, []),
 }
 
@@ -378,6 +383,18 @@ def fkl_pipeline_shapes(p: int) -> list:
         _check(_lib.fkl_pipeline_shape_at(p, k, ctypes.byref(s)))
         out.append(s.as_tuple())
     return out
+
+
+def fkl_pipeline_autotune(p: int, ins: Sequence[fkl_tensor], rois, out: fkl_tensor, stream=None,
+                          reps: int = 5):
+    """Returns (best shape, mean microseconds per launch)."""
+    arr = (fkl_tensor * max(1, len(ins)))(*ins)
+    keep = _rois(rois)
+    best = fkl_launch_shape()
+    us = ctypes.c_float()
+    _check(_lib.fkl_pipeline_autotune(p, len(ins), arr, keep[1] if keep else None, ctypes.byref(out),
+                                      _stream(stream), reps, ctypes.byref(best), ctypes.byref(us)))
+    return best.as_tuple(), us.value
 
 
 class Pipeline:

@@ -9,6 +9,12 @@
 * bf16 / f16 / FP8-E4M3 outputs: |g - round_fmt(o)| <= 1 ulp_fmt(o), i.e. the
   stored value is the correctly rounded oracle value or its neighbour (the
   float32 value fed to the rounding can sit on the other side of a tie).
+  Near zero, where a normalised value comes out of a cancellation
+  (v/255 - mean), the float32 intermediate carries the absolute error the
+  float32 rule allows (1e-6), which can exceed one ulp of the format (f16
+  spacing below 6.1e-5 is 6e-8). There the stored value must be a correct
+  rounding of some value inside the float32 bound:
+  round_fmt(o - d) <= g <= round_fmt(o + d), d = 1e-5 |o| + 1e-6.
 * integer / byte outputs: bit-exact.
 """
 from __future__ import annotations
@@ -52,7 +58,9 @@ def check_lowp(got_values, want, fmt: str, scale: float = 1.0, what=""):
     ref = rnd(o)
     ulp = O.format_ulp(o, fmt)
     err = np.abs(g - ref)
-    bad = err > ulp
+    d = (F32_RTOL * np.abs(o * scale) + F32_ATOL) / scale
+    inside_f32_bound = (g >= rnd(o - d)) & (g <= rnd(o + d))
+    bad = (err > ulp) & ~inside_f32_bound
     assert not bad.any(), (f"{what}: {bad.sum()} of {bad.size} values more than 1 {fmt} ulp from the "
                            f"rounded oracle; worst {err.max():.3g}")
     exact = float(np.mean(err == 0))

@@ -404,3 +404,23 @@ def test_integer_chain_bit_exact_brute_force():
                 val = (7 * (1 + j) + 3 * (2 + i) + 11 * (2 - c)) % 256
                 val = min(255, max(0, val + (100, -50, 0)[c]))
                 assert out[j, i, c] == val
+
+
+# ---------------------------------------------------------------- parity rule itself
+
+
+def test_lowp_rule_accepts_roundings_inside_the_f32_bound_only():
+    import sys, os
+    sys.path.insert(0, os.path.dirname(__file__))
+    from parity import check_lowp
+    o = np.array([8.2607667e-05, 1.0, 0.3])
+    # correct roundings pass
+    check_lowp(O.round_f16(o), o, "f16")
+    # near zero: a rounding of a value 1e-7 away (inside 1e-6) passes
+    check_lowp(O.round_f16(o - np.array([1e-7, 0, 0])), o, "f16")
+    # two ulps away at 1.0 fails
+    with pytest.raises(AssertionError):
+        check_lowp(np.array([O.round_f16(o)[0], 1.0 + 2 * 2.0 ** -10, 0.3]), o, "f16")
+    # a value 1e-5 away near zero fails
+    with pytest.raises(AssertionError):
+        check_lowp(O.round_f16(o - np.array([1e-5, 0, 0])), o, "f16")

@@ -372,3 +372,41 @@ def test_cuda_graph_capture_replays(F, W):
     g.replay()
     torch.cuda.synchronize()
     assert torch.equal(out.view(torch.uint8), ref.view(torch.uint8))
+
+
+def test_vertical_chain_every_shape_bit_exact(F, W):
+    x = synth.f32_uniform(2, 300_001)
+    kinds, consts = synth.chain_constants(2, 21)
+    want = O.vertical_chain_f32(x, kinds, consts).view(np.uint32)
+    p = F.Pipeline(W.vertical_chain(kinds, consts))
+    xin = torch.from_numpy(x).cuda()
+    for shape in F.fkl_pipeline_shapes(p.handle):
+        F.fkl_pipeline_set_shape(p.handle, shape)
+        out = torch.full_like(xin, float("nan"))
+        F.fkl_execute(p.handle, F.as_fkl(xin), F.as_fkl(out))
+        torch.cuda.synchronize()
+        assert np.array_equal(out.cpu().numpy().view(np.uint32), want), shape
+
+
+def test_autotune_keeps_results(F, W):
+    frames = synth.nv12_frames(3, 8, 720, 1280)
+    dev = torch.from_numpy(frames).cuda()
+    p = F.Pipeline(W.nv12_letterbox_chain(F.FKL_BF16))
+    out = torch.zeros((8, 3, 640, 640), dtype=torch.bfloat16, device="cuda")
+    ins = [F.as_fkl(dev[i], F.FKL_LAYOUT_NV12) for i in range(8)]
+    o = F.as_fkl(out, F.FKL_LAYOUT_NCHW)
+    best, us = F.fkl_pipeline_autotune(p.handle, ins, None, o, reps=2)
+    assert best in F.fkl_pipeline_shapes(p.handle) and us > 0
+    assert F.fkl_pipeline_get_shape(p.handle) == best
+    ref, _ = nv12_case(F, W, "bf16", frames)
+    out.zero_()
+    F.fkl_execute_batch(p.handle, ins, None, o)
+    torch.cuda.synchronize()
+    assert torch.equal(out.view(torch.uint8), ref.view(torch.uint8))
+
+    kinds, consts = synth.chain_constants(2, 10)
+    pv = F.Pipeline(W.vertical_chain(kinds, consts))
+    x = torch.from_numpy(synth.f32_uniform(2, 1 << 20)).cuda()
+    y = torch.empty_like(x)
+    best, us = F.fkl_pipeline_autotune(pv.handle, [F.as_fkl(x)], None, F.as_fkl(y), reps=2)
+    assert best in F.fkl_pipeline_shapes(pv.handle)
