@@ -209,6 +209,33 @@ FKL_API fkl_status fkl_execute_batch_unfused(fkl_pipeline p, int32_t n,
                                      fkl_tensor* out, void* workspace,
                                      size_t workspace_bytes, void* stream);
 
+/*
+ * fkl_execute_batch_unfused_static: the unfused form above, for callers that
+ * cannot allocate device memory -- for example a host framework that owns
+ * every device allocation under a fixed memory budget, or a latency-critical
+ * loop where cudaMalloc's implicit device synchronisation is not acceptable.
+ * This call allocates nothing (no cudaMalloc/cudaFree, no host heap): the two
+ * intermediate images live in one 32 MiB array (32 * 2^20 bytes) that the
+ * library declares statically in device memory; every GPU that loads the
+ * library holds it until the process exits. The paper has no counterpart: it
+ * is a service of this library, not part of the fused method.
+ *
+ * Arguments and results are those of fkl_execute_batch_unfused without the
+ * workspace. A batch whose intermediates need more than 32 MiB (the value
+ * fkl_unfused_workspace_bytes reports) is rejected with FKL_ERR_INVALID
+ * before anything is enqueued; vertical chains need no scratch.
+ * The first call on a device looks up the array's device address (once per
+ * device, with that device current); make that first call before any stream
+ * capture. Every call shares the one array and leaves its last contents in
+ * it: nothing needs to start at zero, because each intermediate is written in
+ * full before it is read, but calls whose work overlaps on the GPU (other
+ * streams, other threads) race on it -- order them on one stream or with
+ * events.
+ */
+FKL_API fkl_status fkl_execute_batch_unfused_static(fkl_pipeline p, int32_t n, const fkl_tensor* ins,
+                                                    const int32_t* rois, fkl_tensor* out,
+                                                    void* stream);
+
 /* ------------------------------------------------------------------------ */
 /* Introspection and tuning                                                 */
 /* ------------------------------------------------------------------------ */

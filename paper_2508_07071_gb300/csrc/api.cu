@@ -324,6 +324,38 @@ int sm_count() {
 namespace {
 const int kBlocks[][2] = {{8, 16}, {16, 8}, {16, 16}, {32, 4}, {32, 8}, {64, 2}, {64, 4}, {128, 1}, {128, 2}};
 }
+// ---------------------------------------------------------------------------
+// Scratch for fkl_execute_batch_unfused_static: a fixed device array that
+// every GPU loading this library holds until the process exits. Host code
+// must not pass `g_unfused_scratch` itself to a kernel (on the host that name
+// is only a stand-in); it asks the runtime for the device address instead.
+// ---------------------------------------------------------------------------
+constexpr size_t kStaticScratchBytes = size_t(32) << 20;  // 32 MiB
+static __device__ __align__(256) uint8_t g_unfused_scratch[kStaticScratchBytes];
+
+namespace {
+std::mutex g_scratch_mu;
+void* g_scratch_ptr[64] = {nullptr};
+
+// Device address of g_unfused_scratch on the current device, looked up once
+// per device (the lookup also loads this library's module on that device).
+cudaError_t static_scratch(void** out) {
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  if (dev < 0 || dev >= 64) return cudaErrorInvalidDevice;
+  std::lock_guard<std::mutex> lk(g_scratch_mu);
+  if (!g_scratch_ptr[dev]) {
+    void* ptr = nullptr;
+    e = cudaGetSymbolAddress(&ptr, g_unfused_scratch);
+    if (e != cudaSuccess) return e;
+    g_scratch_ptr[dev] = ptr;
+  }
+  *out = g_scratch_ptr[dev];
+  return cudaSuccess;
+}
+}  // namespace
+
 
 std::vector<fkl_launch_shape> shapes_for(const Spec& s) {
   std::vector<int> vecs;
@@ -644,6 +676,57 @@ fkl_status fkl_pipeline_autotune(fkl_pipeline p, int32_t n, const fkl_tensor* in
   p->shape = best_s;
   if (best) *best = best_s;
   if (best_us) *best_us = best_t;
+  return FKL_OK;
+}
+
+fkl_status fkl_execute_batch_unfused_static(fkl_pipeline p, int32_t n, const fkl_tensor* ins, const int32_t* rois,
+                                            fkl_tensor* out, void* stream) {
+  if (!p) return fail(FKL_ERR_INVALID, "null pipeline");
+  const cudaStream_t s = static_cast<cudaStream_t>(stream);
+  if (p->spec.family == FAM_VCHAIN) {  // one kernel per op, in place on `out`: no scratch
+    if (n != 1) return fail(FKL_ERR_INVALID, "float32 tensor chains take one tensor (n = 1)");
+    int64_t len = 0;
+    const fkl_status st = check_linear(ins, out, len);
+    if (st != FKL_OK) return st;
+    if (len == 0) return FKL_OK;
+    const cudaError_t e =
+        launch_unfused_vchain(p->spec, static_cast<const float*>(ins->data), static_cast<float*>(out->data), len, s);
+    return e == cudaSuccess ? FKL_OK : cuda_fail(e, "unfused launch");
+  }
+  if (n < 0) return fail(FKL_ERR_INVALID, "negative batch size");
+  if (n > 0 && !ins) return fail(FKL_ERR_INVALID, "inputs missing");
+  OutDesc od;
+  fkl_status st = check_out(p->spec, out, n, od);
+  if (st != FKL_OK) return st;
+  // First pass: validate every image and size the two intermediates (no
+  // host or device allocation: one image's parameters at a time).
+  const int64_t elem = p->spec.family == FAM_INT ? 3 : 12;
+  int64_t px = static_cast<int64_t>(od.H) * od.W;
+  for (int i = 0; i < n; ++i) {
+    fkl::ResampleParams r;
+    st = image_params(p->spec, &ins[i], rois, i, od, r);
+    if (st != FKL_OK) return st;
+    if (p->spec.family == FAM_NV12) px = std::max<int64_t>(px, static_cast<int64_t>(r.rw) * r.rh);
+  }
+  const int64_t each = (px * elem + 255) / 256 * 256;
+  if (2 * each > static_cast<int64_t>(kStaticScratchBytes))
+    return fail(FKL_ERR_INVALID,
+                "these images need %lld bytes of scratch; the static scratch holds %zu bytes "
+                "(use fkl_execute_batch_unfused with a caller workspace)",
+                static_cast<long long>(2 * each), kStaticScratchBytes);
+  if (n == 0) return FKL_OK;
+  void* base = nullptr;
+  const cudaError_t ce = static_scratch(&base);
+  if (ce != cudaSuccess) return cuda_fail(ce, "static scratch address");
+  uint8_t* ws0 = static_cast<uint8_t*>(base);
+  uint8_t* ws1 = ws0 + each;
+  for (int i = 0; i < n; ++i) {
+    fkl::ResampleParams r;
+    st = image_params(p->spec, &ins[i], rois, i, od, r);
+    if (st != FKL_OK) return st;
+    const cudaError_t e = launch_unfused_image(p->spec, r, od.p, i, od.H, od.W, ws0, ws1, s);
+    if (e != cudaSuccess) return cuda_fail(e, "unfused launch");
+  }
   return FKL_OK;
 }
 

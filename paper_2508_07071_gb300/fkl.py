@@ -85,6 +85,10 @@ EXPORTS = {
                                                  ctypes.POINTER(ctypes.c_int32),
                                                  ctypes.POINTER(fkl_tensor), ctypes.c_void_p,
                                                  ctypes.c_size_t, ctypes.c_void_p]),
+    "fkl_execute_batch_unfused_static": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int32,
+                                                        ctypes.POINTER(fkl_tensor),
+                                                        ctypes.POINTER(ctypes.c_int32),
+                                                        ctypes.POINTER(fkl_tensor), ctypes.c_void_p]),
     "fkl_pipeline_kernel_name": (ctypes.c_char_p, [ctypes.c_void_p]),
     "fkl_pipeline_get_shape": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(fkl_launch_shape)]),
     "fkl_pipeline_set_shape": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(fkl_launch_shape)]),
@@ -363,6 +367,15 @@ def fkl_execute_batch_unfused(p: int, ins: Sequence[fkl_tensor], rois, out: fkl_
     _check(_lib.fkl_execute_batch_unfused(p, len(ins), arr, keep[1] if keep else None,
                                           ctypes.byref(out), workspace_ptr, workspace_bytes,
                                           _stream(stream)))
+
+
+def fkl_execute_batch_unfused_static(p: int, ins: Sequence[fkl_tensor], rois, out: fkl_tensor,
+                                     stream=None) -> None:
+    """Unfused form on the library's static device scratch (no allocation)."""
+    arr = (fkl_tensor * max(1, len(ins)))(*ins)
+    keep = _rois(rois)
+    _check(_lib.fkl_execute_batch_unfused_static(p, len(ins), arr, keep[1] if keep else None,
+                                                 ctypes.byref(out), _stream(stream)))
 
 
 def fkl_pipeline_get_shape(p: int) -> tuple:
