@@ -278,8 +278,11 @@ def run_ours(args):
         elif not args.no_autotune:
             ins = wl.ins if hasattr(wl, "ins") else [wl.i]
             rois = getattr(wl, "rois", None)
+            fl = getattr(wl, "flush", None)
             best, us = F.fkl_pipeline_autotune(wl.pipe.handle, ins, rois, wl.o, stream=stream,
-                                               reps=args.autotune_reps)
+                                               reps=args.autotune_reps,
+                                               flush_ptr=fl.data_ptr() if fl is not None else 0,
+                                               flush_bytes=fl.numel() if fl is not None else 0)
             tuned = {"shape": list(best), "us_per_launch": round(us, 2),
                      "candidates": len(F.fkl_pipeline_shapes(wl.pipe.handle))}
         for _ in range(args.warmup):
@@ -443,7 +446,7 @@ def main():
     ap.add_argument("--cpu-seconds", type=float, default=10.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-autotune", action="store_true")
-    ap.add_argument("--autotune-reps", type=int, default=3)
+    ap.add_argument("--autotune-reps", type=int, default=7)
     ap.add_argument("--shape", default="", help="vec,tx,ty,ry launch shape (skips the autotuner)")
     args = ap.parse_args()
     if args.warmup < 3:

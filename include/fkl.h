@@ -271,15 +271,24 @@ FKL_API fkl_status fkl_pipeline_shape_at(fkl_pipeline p, int32_t k,
 /*
  * Autotuner (tile, coarsening and block shape): runs every launch shape
  * fkl_pipeline_shape_at lists on these arguments -- one warm-up launch, then
- * `reps` launches timed with CUDA events on `stream` -- and keeps the fastest
- * as the pipeline's shape. `best` and `best_us` (mean microseconds per launch,
- * may be NULL) report it. Every trial writes `out`. Synchronises `stream`;
+ * `reps` (1..32) launches enqueued back to back, each timed with its own pair
+ * of CUDA events on `stream` -- and keeps the shape with the lowest median
+ * as the pipeline's shape. `best` and `best_us` (median microseconds per
+ * launch, may be NULL) report it. Every trial writes `out`. Synchronises `stream`;
  * not capturable in a CUDA graph. A pipeline with a single shape returns it
  * without timing.
+ * fkl_pipeline_autotune_flushed: the same, but before every timed launch it
+ * overwrites `flush` (caller-owned device memory, `flush_bytes` bytes, best
+ * larger than the L2 cache) with cudaMemsetAsync outside the timed interval,
+ * so that inputs smaller than L2 are tuned from a cold cache.
  */
 FKL_API fkl_status fkl_pipeline_autotune(fkl_pipeline p, int32_t n, const fkl_tensor* ins,
                                          const int32_t* rois, fkl_tensor* out, void* stream,
                                          int32_t reps, fkl_launch_shape* best, float* best_us);
+FKL_API fkl_status fkl_pipeline_autotune_flushed(fkl_pipeline p, int32_t n, const fkl_tensor* ins,
+                                                 const int32_t* rois, fkl_tensor* out, void* stream,
+                                                 int32_t reps, void* flush, size_t flush_bytes,
+                                                 fkl_launch_shape* best, float* best_us);
 
 /* Library version string. */
 FKL_API const char* fkl_version(void);

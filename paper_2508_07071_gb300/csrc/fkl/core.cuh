@@ -79,6 +79,12 @@ FKL_HD Tuple<H, Ts...> make_tuple(const H& h, const Ts&... xs) {
   return Tuple<H, Ts...>{h, make_tuple(xs...)};
 }
 
+// (h, t...) from h and the tuple (t...).
+template <class H, class... Ts>
+FKL_HD Tuple<H, Ts...> prepend(const H& h, const Tuple<Ts...>& t) {
+  return Tuple<H, Ts...>{h, t};
+}
+
 // Apply one compute IOp, choosing the exec form from its InstanceType at
 // compile time (paper §IV-C, "if constexpr" on InstanceType).
 template <class I, class T>
@@ -145,6 +151,43 @@ FKL_D uint32_t pack2_e4m3(float lo, float hi) {
   uint16_t r;
   asm("cvt.rn.satfinite.e4m3x2.f32 %0, %1, %2;" : "=h"(r) : "f"(hi), "f"(lo));
   return static_cast<uint32_t>(r);
+}
+
+// ---------------------------------------------------------------------------
+// Packed float pairs: two independent IEEE binary32 lanes per instruction
+// (add/mul/fma .rn .f32x2, sm_100 and later). Each lane rounds exactly like
+// the scalar __fadd_rn/__fmul_rn/__fmaf_rn, so packed and scalar code give
+// the same bits.
+// ---------------------------------------------------------------------------
+struct F2 {
+  unsigned long long v;
+};
+FKL_D F2 f2(float lo, float hi) {
+  F2 r;
+  asm("mov.b64 %0, {%1, %2};" : "=l"(r.v) : "f"(lo), "f"(hi));
+  return r;
+}
+FKL_D F2 f2s(float x) { return f2(x, x); }
+FKL_D void f2split(F2 a, float& lo, float& hi) { asm("mov.b64 {%0, %1}, %2;" : "=f"(lo), "=f"(hi) : "l"(a.v)); }
+FKL_D F2 f2add(F2 a, F2 b) {
+  F2 d;
+  asm("add.rn.f32x2 %0, %1, %2;" : "=l"(d.v) : "l"(a.v), "l"(b.v));
+  return d;
+}
+FKL_D F2 f2sub(F2 a, F2 b) {
+  F2 d;
+  asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(d.v) : "l"(a.v), "l"(b.v));
+  return d;
+}
+FKL_D F2 f2mul(F2 a, F2 b) {
+  F2 d;
+  asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(d.v) : "l"(a.v), "l"(b.v));
+  return d;
+}
+FKL_D F2 f2fma(F2 a, F2 b, F2 c) {
+  F2 d;
+  asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(d.v) : "l"(a.v), "l"(b.v), "l"(c.v));
+  return d;
 }
 
 template <class OutT>

@@ -32,7 +32,8 @@ struct ResampleParams {
 };
 static_assert(sizeof(ResampleParams) == 64, "kernel-parameter table entry");
 
-constexpr int32_t kFast2x = 1;
+constexpr int32_t kFast2x = 1;   // exact 2x, even 16-byte aligned window: vector loads
+constexpr int32_t kExact2x = 2;  // rw == 2 dw and rh == 2 dh
 
 // Half-pixel sample along one axis for output index d (0 <= d < n_dst):
 // u = (d + 1/2) n_src / n_dst - 1/2 = num / D with num = (2d+1) n_src - n_dst
@@ -85,8 +86,10 @@ struct AxisWalker {
   }
 };
 
-// Bilinear blend of four float taps with weights w / D computed by IEEE
-// division (exact whenever the ratio is representable, e.g. 1/2).
+// Bilinear blend of four float taps (tRC: row R, column C) with weights
+// w / D computed by IEEE division (exact whenever the ratio is representable,
+// e.g. 1/2). Each column is blended vertically first, then the two columns
+// horizontally; every path of this library uses that order.
 FKL_D F3 blend_float(const F3& t00, const F3& t01, const F3& t10, const F3& t11,
                      const AxisTap& tx, int Dx, const AxisTap& ty, int Dy) {
   const float ax1 = __fdiv_rn(static_cast<float>(tx.w1), static_cast<float>(Dx));
@@ -96,9 +99,9 @@ FKL_D F3 blend_float(const F3& t00, const F3& t01, const F3& t10, const F3& t11,
   F3 o;
 #pragma unroll
   for (int c = 0; c < 3; ++c) {
-    const float top = __fadd_rn(__fmul_rn(ax0, t00.v[c]), __fmul_rn(ax1, t01.v[c]));
-    const float bot = __fadd_rn(__fmul_rn(ax0, t10.v[c]), __fmul_rn(ax1, t11.v[c]));
-    o.v[c] = __fadd_rn(__fmul_rn(ay0, top), __fmul_rn(ay1, bot));
+    const float left = __fadd_rn(__fmul_rn(ay0, t00.v[c]), __fmul_rn(ay1, t10.v[c]));
+    const float right = __fadd_rn(__fmul_rn(ay0, t01.v[c]), __fmul_rn(ay1, t11.v[c]));
+    o.v[c] = __fadd_rn(__fmul_rn(ax0, left), __fmul_rn(ax1, right));
   }
   return o;
 }
@@ -217,13 +220,26 @@ FKL_D F3 yuv_to_rgb(float yf, const ChromaTerms& t) {
   return o;
 }
 
-// Byte k of a 32-bit word as an exact float minus `bias`: the byte is placed
-// in the mantissa of 2^23 and the 2^23 is subtracted along with the bias.
-FKL_D float byte_minus(uint32_t w, int k, float bias_plus_2p23) {
-  const uint32_t f = __byte_perm(w, 0x4B000000u, 0x7440u | static_cast<uint32_t>(k));
-  return __fsub_rn(__uint_as_float(f), bias_plus_2p23);
-}
 constexpr float k2p23 = 8388608.f;
+
+// 2^23 + (byte k of w), exactly, as a float: the byte is placed in the
+// mantissa of 2^23 by one byte permute; subtracting 2^23 + bias later gives
+// byte - bias exactly.
+FKL_D float byte_as_float(uint32_t w, int k) {
+  return __uint_as_float(__byte_perm(w, 0x4B000000u, 0x7440u | static_cast<uint32_t>(k)));
+}
+
+// yuv_to_rgb on a pair of luma samples (one per lane) with their chroma terms.
+FKL_D void rgb_pair(F2 yf, F2 cy, F2 rv, F2 guv, F2 bu, F2 c255, F2 (&o)[3]) {
+  float l0, l1, r0, r1, g0, g1, b0, b1;
+  f2split(f2mul(cy, yf), l0, l1);
+  f2split(rv, r0, r1);
+  f2split(guv, g0, g1);
+  f2split(bu, b0, b1);
+  o[0] = f2mul(f2(add_sat(l0, r0), add_sat(l1, r1)), c255);
+  o[1] = f2mul(f2(sub_sat(l0, g0), sub_sat(l1, g1)), c255);
+  o[2] = f2mul(f2(add_sat(l0, b0), add_sat(l1, b1)), c255);
+}
 
 // One decoded NV12 sample at absolute source coordinates (sx, sy): nearest
 // (co-sited) chroma sample (sx/2, sy/2), U then V.
@@ -258,8 +274,10 @@ struct ResizeNV12 {
   // Exact 2x downscale of an even-aligned window: output k of the span is
   // the mean of the 2x2 block that shares chroma sample k, so the span reads
   // 2V luma bytes from each of two rows and 2V chroma bytes, all as 16-byte
-  // vectors. The result equals exec() bit for bit: with weights 1/2 the
-  // blend is fl(fl(t00 + t01) + fl(t10 + t11)) / 4.
+  // vectors. Outputs are processed in pairs, one per lane of the packed
+  // f32x2 instructions; only the saturating adds are scalar. The result
+  // equals exec() bit for bit: per lane the same IEEE operations run in the
+  // same order, and with weights 1/2 the blend is fl(fl(t00 + t10) + fl(t01 + t11)) / 4.
   template <int V>
   static FKL_D void span_fast2x(const ParamsType& p, int lx, int ly, F3 (&out)[V]) {
     static_assert(V % 8 == 0, "2x path reads 16-byte vectors");
@@ -275,24 +293,31 @@ struct ResizeNV12 {
       b[i] = __ldg(r1 + i);
       c[i] = __ldg(rc + i);
     }
+    const F2 kY = f2s(k2p23 + 16.f), kC = f2s(k2p23 + 128.f);
+    const F2 cy = f2s(Bt601::cy), crv = f2s(Bt601::crv), cgu = f2s(Bt601::cgu), cgv = f2s(Bt601::cgv),
+             cbu = f2s(Bt601::cbu), c255 = f2s(255.f), quarter = f2s(0.25f);
 #pragma unroll
-    for (int k = 0; k < V; ++k) {
-      // output k uses bytes 2k, 2k+1 of each row: word (2k)/4 = k/2 of the
-      // 16-byte vector k/8, bytes (2k)%4 and (2k)%4 + 1.
-      const int vi = k / 8, wi = (k % 8) / 2, bi = (2 * k) % 4;
+    for (int k = 0; k < V; k += 2) {
+      // outputs k, k+1 use bytes 2k .. 2k+3 of each row: word (k % 8) / 2 of
+      // vector k / 8 holds [left(k), right(k), left(k+1), right(k+1)] for
+      // luma and [U(k), V(k), U(k+1), V(k+1)] for chroma.
+      const int vi = k / 8, wi = (k % 8) / 2;
       const uint32_t wa = reinterpret_cast<const uint32_t*>(&a[vi])[wi];
       const uint32_t wb = reinterpret_cast<const uint32_t*>(&b[vi])[wi];
       const uint32_t wc = reinterpret_cast<const uint32_t*>(&c[vi])[wi];
-      const ChromaTerms ct =
-          chroma_terms(byte_minus(wc, bi, k2p23 + 128.f), byte_minus(wc, bi + 1, k2p23 + 128.f));
-      const F3 t00 = yuv_to_rgb(byte_minus(wa, bi, k2p23 + 16.f), ct);
-      const F3 t01 = yuv_to_rgb(byte_minus(wa, bi + 1, k2p23 + 16.f), ct);
-      const F3 t10 = yuv_to_rgb(byte_minus(wb, bi, k2p23 + 16.f), ct);
-      const F3 t11 = yuv_to_rgb(byte_minus(wb, bi + 1, k2p23 + 16.f), ct);
+      const F2 u = f2sub(f2(byte_as_float(wc, 0), byte_as_float(wc, 2)), kC);
+      const F2 v = f2sub(f2(byte_as_float(wc, 1), byte_as_float(wc, 3)), kC);
+      const F2 rv = f2mul(crv, v), guv = f2fma(cgu, u, f2mul(cgv, v)), bu = f2mul(cbu, u);
+      F2 t[4][3];  // taps row 0 left, row 0 right, row 1 left, row 1 right
+      rgb_pair(f2sub(f2(byte_as_float(wa, 0), byte_as_float(wa, 2)), kY), cy, rv, guv, bu, c255, t[0]);
+      rgb_pair(f2sub(f2(byte_as_float(wa, 1), byte_as_float(wa, 3)), kY), cy, rv, guv, bu, c255, t[1]);
+      rgb_pair(f2sub(f2(byte_as_float(wb, 0), byte_as_float(wb, 2)), kY), cy, rv, guv, bu, c255, t[2]);
+      rgb_pair(f2sub(f2(byte_as_float(wb, 1), byte_as_float(wb, 3)), kY), cy, rv, guv, bu, c255, t[3]);
 #pragma unroll
       for (int ch = 0; ch < 3; ++ch) {
-        const float s = __fadd_rn(__fadd_rn(t00.v[ch], t01.v[ch]), __fadd_rn(t10.v[ch], t11.v[ch]));
-        out[k].v[ch] = __fmul_rn(s, 0.25f);
+        const F2 left = f2add(t[0][ch], t[2][ch]);
+        const F2 right = f2add(t[1][ch], t[3][ch]);
+        f2split(f2mul(f2add(left, right), quarter), out[k].v[ch], out[k + 1].v[ch]);
       }
     }
   }
@@ -308,6 +333,49 @@ struct ResizeNV12 {
     if constexpr (V % 8 == 0) {
       if ((p.flags & kFast2x) && lx >= 0 && lx + V <= p.dw && ((2 * lx) & 15) == 0) {
         span_fast2x<V>(p, lx, ly, out);
+        return;
+      }
+    }
+#pragma unroll
+    for (int k = 0; k < V; ++k) out[k] = exec(Point{pt.x + k, pt.y, pt.z}, p);
+  }
+};
+
+// NV12 -> RGB -> exact 2x downscale (rw = 2 dw, rh = 2 dh) -> placement: a
+// specialisation of ResizeNV12 with no division in it. Every output is the
+// mean of one 2x2 block, fl(fl(t00 + t10) + fl(t01 + t11)) * 1/4, which is
+// what the general bilinear blend computes bit for bit when all weights are 1/2.
+struct ResizeNV12x2 {
+  using InstanceType = ReadType;
+  using ParamsType = ResampleParams;
+  using OutputType = F3;
+
+  static FKL_D F3 exec(const Point& pt, const ParamsType& p) {
+    const int lx = pt.x - p.ox, ly = pt.y - p.oy;
+    if (lx < 0 || ly < 0 || lx >= p.dw || ly >= p.dh) return F3{{p.pad, p.pad, p.pad}};
+    const int sx = p.rx + 2 * lx, sy = p.ry + 2 * ly;
+    const F3 t00 = nv12_sample(p, sx, sy);
+    const F3 t01 = nv12_sample(p, sx + 1, sy);
+    const F3 t10 = nv12_sample(p, sx, sy + 1);
+    const F3 t11 = nv12_sample(p, sx + 1, sy + 1);
+    F3 o;
+#pragma unroll
+    for (int c = 0; c < 3; ++c)
+      o.v[c] = __fmul_rn(__fadd_rn(__fadd_rn(t00.v[c], t10.v[c]), __fadd_rn(t01.v[c], t11.v[c])), 0.25f);
+    return o;
+  }
+
+  template <int V>
+  static FKL_D void exec_span(const Point& pt, const ParamsType& p, F3 (&out)[V]) {
+    const int lx = pt.x - p.ox, ly = pt.y - p.oy;
+    if (ly < 0 || ly >= p.dh) {
+#pragma unroll
+      for (int k = 0; k < V; ++k) out[k] = F3{{p.pad, p.pad, p.pad}};
+      return;
+    }
+    if constexpr (V % 8 == 0) {
+      if ((p.flags & kFast2x) && lx >= 0 && lx + V <= p.dw && ((2 * lx) & 15) == 0) {
+        ResizeNV12::span_fast2x<V>(p, lx, ly, out);
         return;
       }
     }

@@ -34,11 +34,13 @@ struct VecSet<fkl::e4m3_t, true> {
   static constexpr int v[] = {8, 16};
 };
 
-template <class ROp, class OutT, bool kSplit, bool kSwap, int V, int RY, int CAP>
-cudaError_t run_float_chain(const LaunchCtx& c) {
-  using RB = fkl::BatchRead<ROp, CAP>;
-  using W = std::conditional_t<kSplit, fkl::WriteSplit<OutT>, fkl::WritePacked<OutT>>;
-  const Spec& s = *c.spec;
+// Compute ops after the optional swap, fixed at compile time so that an
+// absent op costs nothing: 0 = Mul; 1 = Mul, Sub; 2 = Mul, Sub, Div.
+// (An absent Mul or Sub inside a tail is bound as its exact identity.)
+inline int tail_of(const Spec& s) { return s.has_div ? 2 : (s.has_sub ? 1 : 0); }
+
+template <int kTail>
+auto make_tail(const Spec& s) {
   fkl::IOp<fkl::Mul3> mul;
   fkl::IOp<fkl::Sub3> sub;
   fkl::IOp<fkl::Div3> div;
@@ -47,12 +49,27 @@ cudaError_t run_float_chain(const LaunchCtx& c) {
     sub.params.c[k] = s.sub[k];
     div.params.c[k] = s.div[k];
   }
-  div.params.on = s.has_div ? 1 : 0;
+  div.params.on = 1;
+  if constexpr (kTail == 0) {
+    return fkl::make_tuple(mul);
+  } else if constexpr (kTail == 1) {
+    return fkl::make_tuple(mul, sub);
+  } else {
+    return fkl::make_tuple(mul, sub, div);
+  }
+}
+
+template <class ROp, class OutT, bool kSplit, bool kSwap, int kTail, int V, int RY>
+cudaError_t run_float_chain(const LaunchCtx& c) {
+  using RB = fkl::BatchRead<ROp, kBatchCap>;
+  using W = std::conditional_t<kSplit, fkl::WriteSplit<OutT>, fkl::WritePacked<OutT>>;
+  const Spec& s = *c.spec;
+  auto tail = make_tail<kTail>(s);
   auto cops = [&] {
     if constexpr (kSwap) {
-      return fkl::make_tuple(fkl::IOp<fkl::SwapRB<fkl::F3>>{}, mul, sub, div);
+      return fkl::prepend(fkl::IOp<fkl::SwapRB<fkl::F3>>{}, tail);
     } else {
-      return fkl::make_tuple(mul, sub, div);
+      return tail;
     }
   }();
   using Cops = decltype(cops);
@@ -67,25 +84,20 @@ cudaError_t run_float_chain(const LaunchCtx& c) {
   return fkl::launch_transform2d<V, RY>(a, c.n, c.shape.tx, c.shape.ty, c.stream);
 }
 
-template <class ROp, class OutT, bool kSplit, bool kSwap, int V>
+template <class ROp, class OutT, bool kSplit, bool kSwap, int kTail, int V>
 cudaError_t float_by_ry(const LaunchCtx& c) {
-  const bool single = c.n <= 1;
-  if (c.shape.ry == 1)
-    return single ? run_float_chain<ROp, OutT, kSplit, kSwap, V, 1, 1>(c)
-                  : run_float_chain<ROp, OutT, kSplit, kSwap, V, 1, kBatchCap>(c);
+  if (c.shape.ry == 1) return run_float_chain<ROp, OutT, kSplit, kSwap, kTail, V, 1>(c);
   if constexpr (V <= 8) {  // two rows of 16 pixels would not fit in registers
-    if (c.shape.ry == 2)
-      return single ? run_float_chain<ROp, OutT, kSplit, kSwap, V, 2, 1>(c)
-                    : run_float_chain<ROp, OutT, kSplit, kSwap, V, 2, kBatchCap>(c);
+    if (c.shape.ry == 2) return run_float_chain<ROp, OutT, kSplit, kSwap, kTail, V, 2>(c);
   }
   return cudaErrorInvalidConfiguration;
 }
 
-template <class ROp, class OutT, bool kSplit, bool kSwap, size_t... I>
+template <class ROp, class OutT, bool kSplit, bool kSwap, int kTail, size_t... I>
 cudaError_t float_by_vec(const LaunchCtx& c, std::index_sequence<I...>) {
   cudaError_t err = cudaErrorInvalidConfiguration;
   const bool hit = ((c.shape.vec == VecSet<OutT, kSplit>::v[I]
-                         ? (err = float_by_ry<ROp, OutT, kSplit, kSwap, VecSet<OutT, kSplit>::v[I]>(c), true)
+                         ? (err = float_by_ry<ROp, OutT, kSplit, kSwap, kTail, VecSet<OutT, kSplit>::v[I]>(c), true)
                          : false) ||
                     ...);
   (void)hit;
@@ -95,7 +107,14 @@ cudaError_t float_by_vec(const LaunchCtx& c, std::index_sequence<I...>) {
 template <class ROp, class OutT, bool kSplit, bool kSwap>
 cudaError_t float_by_type(const LaunchCtx& c) {
   constexpr size_t n = sizeof(VecSet<OutT, kSplit>::v) / sizeof(int);
-  return float_by_vec<ROp, OutT, kSplit, kSwap>(c, std::make_index_sequence<n>{});
+  switch (tail_of(*c.spec)) {
+    case 0:
+      return float_by_vec<ROp, OutT, kSplit, kSwap, 0>(c, std::make_index_sequence<n>{});
+    case 1:
+      return float_by_vec<ROp, OutT, kSplit, kSwap, 1>(c, std::make_index_sequence<n>{});
+    default:
+      return float_by_vec<ROp, OutT, kSplit, kSwap, 2>(c, std::make_index_sequence<n>{});
+  }
 }
 
 // Entry for one (ROp, output type): picks the packed/split writer and the

@@ -1,9 +1,13 @@
-// Compiled float chains over NV12 frames (BT.601 decode, crop, bilinear resize, letterbox),
-// writing f16 outputs.
+// Compiled float chains over NV12 frames (BT.601 decode, crop, bilinear resize,
+// letterbox), writing f16 outputs. Launches whose images are all exact 2x
+// downscales use the division-free ResizeNV12x2 read op.
 #include "float_family.cuh"
 
 namespace fkl_impl {
 
-cudaError_t launch_nv12_f16(const LaunchCtx& c) { return float_dispatch_type<fkl::ResizeNV12, fkl::f16_t>(c); }
+cudaError_t launch_nv12_f16(const LaunchCtx& c) {
+  return c.all_exact2x ? float_dispatch_type<fkl::ResizeNV12x2, fkl::f16_t>(c)
+                       : float_dispatch_type<fkl::ResizeNV12, fkl::f16_t>(c);
+}
 
 }  // namespace fkl_impl

@@ -46,6 +46,7 @@ struct LaunchCtx {
   fkl::OutParams out;
   int H, W;
   cudaStream_t stream;
+  bool all_exact2x;  // every image of the launch is an exact 2x downscale
 };
 
 // Fused launches of the float image families, one translation unit per

@@ -100,6 +100,13 @@ EXPORTS = {
                                              ctypes.c_void_p, ctypes.c_int32,
                                              ctypes.POINTER(fkl_launch_shape),
                                              ctypes.POINTER(ctypes.c_float)]),
+    "fkl_pipeline_autotune_flushed": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int32,
+                                                     ctypes.POINTER(fkl_tensor),
+                                                     ctypes.POINTER(ctypes.c_int32),
+                                                     ctypes.POINTER(fkl_tensor), ctypes.c_void_p,
+                                                     ctypes.c_int32, ctypes.c_void_p, ctypes.c_size_t,
+                                                     ctypes.POINTER(fkl_launch_shape),
+                                                     ctypes.POINTER(ctypes.c_float)]),
     "fkl_version": (ctypes.c_char_p, []),
 }
 
@@ -399,14 +406,20 @@ def fkl_pipeline_shapes(p: int) -> list:
 
 
 def fkl_pipeline_autotune(p: int, ins: Sequence[fkl_tensor], rois, out: fkl_tensor, stream=None,
-                          reps: int = 5):
-    """Returns (best shape, mean microseconds per launch)."""
+                          reps: int = 5, flush_ptr: int = 0, flush_bytes: int = 0):
+    """Returns (best shape, median microseconds per launch). With a flush
+    buffer, every timed launch starts from a cold L2."""
     arr = (fkl_tensor * max(1, len(ins)))(*ins)
     keep = _rois(rois)
     best = fkl_launch_shape()
     us = ctypes.c_float()
-    _check(_lib.fkl_pipeline_autotune(p, len(ins), arr, keep[1] if keep else None, ctypes.byref(out),
-                                      _stream(stream), reps, ctypes.byref(best), ctypes.byref(us)))
+    if flush_bytes:
+        _check(_lib.fkl_pipeline_autotune_flushed(p, len(ins), arr, keep[1] if keep else None,
+                                                  ctypes.byref(out), _stream(stream), reps, flush_ptr,
+                                                  flush_bytes, ctypes.byref(best), ctypes.byref(us)))
+    else:
+        _check(_lib.fkl_pipeline_autotune(p, len(ins), arr, keep[1] if keep else None, ctypes.byref(out),
+                                          _stream(stream), reps, ctypes.byref(best), ctypes.byref(us)))
     return best.as_tuple(), us.value
 
 
