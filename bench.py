@@ -99,15 +99,36 @@ class NV12Letterbox(Workload):
         per = (nv12 + rgb) + (rgb + img) + (2 * img) + (img + self.out * self.out * 3 * self.el)
         return self.n * per
 
-    def e2e_setup(self):
-        torch = self.torch
+    def e2e_setup(self, chunk=32, depth=3):
+        """Pinned host frames in, pinned host planes out, through the
+        library's overlapped host executor (fkl_execute_batch_host)."""
+        torch, F = self.torch, self.F
         self.host_in = torch.from_numpy(self.frames_host).pin_memory()
         self.host_out = torch.empty(self.dst.shape, dtype=self.dst.dtype).pin_memory()
+        self.host_ins = [F.as_fkl(self.host_in[i], F.FKL_LAYOUT_NV12) for i in range(self.n)]
+        self.host_o = F.as_fkl(self.host_out, F.FKL_LAYOUT_NCHW)
+        self.executor = F.fkl_host_executor_create(self.pipe.handle, chunk, depth, self.h * 3 // 2 * self.w,
+                                                   3 * self.out * self.out * self.el)
+        self.e2e_launches = (self.n + chunk - 1) // chunk
+        self.e2e_note = f"fkl_execute_batch_host, chunks of {chunk} frames, {depth} device slots"
 
     def e2e_step(self, stream):
-        self.frames.copy_(self.host_in, non_blocking=True)
-        self.step(stream)
-        self.host_out.copy_(self.dst, non_blocking=True)
+        self.F.fkl_execute_batch_host(self.executor, self.host_ins, None, self.host_o, stream=stream)
+
+    def link_copy(self, stream):
+        """The step's host<->device bytes alone: H2D of the frames and D2H of
+        the planes on two streams at once (the e2e ceiling of this link)."""
+        torch = self.torch
+        if not hasattr(self, "_s2"):
+            self._s2 = torch.cuda.Stream()
+        e = torch.cuda.Event()
+        e.record(stream)
+        self._s2.wait_event(e)
+        with torch.cuda.stream(stream):
+            self.frames.copy_(self.host_in, non_blocking=True)
+        with torch.cuda.stream(self._s2):
+            self.host_out.copy_(self.dst, non_blocking=True)
+        stream.wait_event(self._s2.record_event())
 
     def oracle_sample(self, O, k):
         O.preprocess_nv12(self.frames_host[k % self.n], self.out, self.out, pad=114.0, mul=1 / 255)
@@ -278,11 +299,8 @@ def run_ours(args):
         elif not args.no_autotune:
             ins = wl.ins if hasattr(wl, "ins") else [wl.i]
             rois = getattr(wl, "rois", None)
-            fl = getattr(wl, "flush", None)
             best, us = F.fkl_pipeline_autotune(wl.pipe.handle, ins, rois, wl.o, stream=stream,
-                                               reps=args.autotune_reps,
-                                               flush_ptr=fl.data_ptr() if fl is not None else 0,
-                                               flush_bytes=fl.numel() if fl is not None else 0)
+                                               reps=args.autotune_reps, before=between)
             tuned = {"shape": list(best), "us_per_launch": round(us, 2),
                      "candidates": len(F.fkl_pipeline_shapes(wl.pipe.handle))}
         for _ in range(args.warmup):
@@ -317,13 +335,17 @@ def run_ours(args):
 
         # end to end through the public call with host buffers
         ke = min(args.steps, args.e2e_steps)
-        e2e_ms = None
+        e2e_ms = link_ms = None
         if ke > 0:
             wl.e2e_setup()
             for _ in range(2):
                 wl.e2e_step(stream)
             torch.cuda.synchronize()
             e2e_ms = float(np.mean(time_steps(torch, wl.e2e_step, ke, stream)))
+            link_ms = None
+            if hasattr(wl, "link_copy"):
+                wl.link_copy(stream)
+                link_ms = float(np.mean(time_steps(torch, wl.link_copy, ke, stream)))
 
     peak, peak_kind = measured_peaks()
     total_bytes = wl.bytes * world
@@ -360,7 +382,10 @@ def run_ours(args):
         "e2e": None if e2e_ms is None else {
             "value": round(wl.bytes * world / (e2e_ms * 1e-3) / 1e9, 1), "unit": "GB/s",
             "ms_per_step": round(e2e_ms, 4), "h2d_bytes_per_step": int(wl.h2d_bytes),
-            "d2h_bytes_per_step": int(wl.d2h_bytes), "steps": ke},
+            "d2h_bytes_per_step": int(wl.d2h_bytes), "steps": ke,
+            "path": getattr(wl, "e2e_note", "torch pinned copies + fkl_execute_batch on one stream"),
+            "link_copy_ms": None if link_ms is None else round(link_ms, 4),
+            "frac_of_link": None if link_ms is None else round(link_ms / e2e_ms, 3)},
         "gpu_launches": int(args.steps * wl.launches_per_step),
         "clocks": sampler.summary(),
         "wall_s_timed": round(wall, 4),
@@ -388,6 +413,72 @@ def cpu_baseline(wl, args, budget_s=None):
     return {"value": round(nbytes / dt / 1e9, 6), "unit": "GB/s", "cores": 1, "kind": "oracle",
             "sample": f"{k} unit(s) of the workload (images/frames, or 1M-element slices), "
                       f"{dt:.1f} s, float64 numpy, single thread"}
+
+
+def run_serve(args):
+    """Serving loop: Poisson arrivals of requests of 1-64 images of mixed
+    sizes (320-3840 x 240-2160) through fkl_server_*, full-frame resize to
+    224x224 -> RGB -> normalise -> planar FP16. Latency = completion minus
+    scheduled arrival (copies to the device included)."""
+    import torch
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_2508_07071_gb300 import fkl as F, synth, workloads as W
+
+    rng = np.random.default_rng(4)
+    pool = []
+    for k in range(args.pool):
+        w, h = int(rng.integers(320, 3841)), int(rng.integers(240, 2161))
+        pool.append(torch.from_numpy(synth.packed_image(1000 + k, h, w)).pin_memory())
+    reqs = [list(rng.integers(0, len(pool), int(rng.integers(1, 65)))) for _ in range(args.requests)]
+    pipe = F.Pipeline(W.normalize_chain(224, 224, out_dtype=F.FKL_F16))
+    fk = [[F.as_fkl(pool[i]) for i in r] for r in reqs]
+    results = []
+    for rate in [float(x) for x in args.rates.split(",")]:
+        arrivals = synth.poisson_arrivals(4, rate, len(reqs))
+        for mode, mname in ((F.FKL_SERVE_PERSISTENT, "persistent"), (F.FKL_SERVE_UNFUSED, "unfused_per_request")):
+            srv = F.fkl_server_create(pipe.handle, mode, max_inflight=args.slots, arena_bytes=args.arena_gb << 30)
+            try:
+                # warm-up: one request through the server
+                rid = F.fkl_server_submit(srv, fk[0])
+                F.fkl_server_wait(srv, rid, 60000)
+                F.fkl_server_release(srv, rid)
+                t0 = time.monotonic() + 0.01
+                live, lat, q, h2d, nimg = {}, [], [], [], 0
+                i = 0
+                t_last = t0
+                while i < len(reqs) or live:
+                    now = time.monotonic()
+                    while i < len(reqs) and t0 + arrivals[i] <= now:
+                        live[F.fkl_server_submit(srv, fk[i])] = t0 + arrivals[i]
+                        i += 1
+                    for rid in list(live):
+                        done, _ = F.fkl_server_poll(srv, rid)
+                        if done:
+                            info = F.fkl_server_request_info(srv, rid)
+                            lat.append(info.t_done - live.pop(rid))
+                            q.append(info.t_admit - info.t_submit)
+                            h2d.append(info.t_ready - info.t_admit)
+                            nimg += info.n_images
+                            t_last = max(t_last, info.t_done)
+                            F.fkl_server_release(srv, rid)
+                    time.sleep(0.0001)
+                st = F.fkl_server_get_stats(srv)
+            finally:
+                F.fkl_server_destroy(srv)
+            lat_ms = np.array(lat) * 1e3
+            results.append({"rate_req_s": rate, "mode": mname, "requests": len(reqs), "images": nimg,
+                            "p50_ms": round(float(np.percentile(lat_ms, 50)), 3),
+                            "p99_ms": round(float(np.percentile(lat_ms, 99)), 3),
+                            "queue_p50_ms": round(float(np.median(q)) * 1e3, 3),
+                            "h2d_p50_ms": round(float(np.median(h2d)) * 1e3, 3),
+                            "images_per_s": round(nimg / (t_last - t0), 1),
+                            "kernel_launches": int(st.kernel_launches),
+                            "arena_peak_gb": round(st.arena_peak_bytes / 2**30, 3)})
+            print(json.dumps(results[-1]), flush=True)
+    print(json.dumps({"metric": "serving latency and throughput", "workload": "Poisson requests, 1-64 u8 BGR "
+                      "images 320-3840 x 240-2160 -> 224x224 RGB normalised planar f16", "results": results}),
+          flush=True)
 
 
 def run_reference(args):
@@ -437,7 +528,12 @@ def main():
     ap.add_argument("--steps", type=int, default=200)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="nv12", choices=["nv12", "single", "hf", "vchain"])
+    ap.add_argument("--workload", default="nv12", choices=["nv12", "single", "hf", "vchain", "serve"])
+    ap.add_argument("--rates", default="200,500,1000,2000", help="serve: request rates (req/s)")
+    ap.add_argument("--requests", type=int, default=200, help="serve: requests per rate")
+    ap.add_argument("--pool", type=int, default=48, help="serve: distinct host images")
+    ap.add_argument("--slots", type=int, default=64, help="serve: request slots")
+    ap.add_argument("--arena-gb", type=int, default=16, help="serve: device arena (GiB)")
     ap.add_argument("--out-dtype", default="bf16", choices=["bf16", "f16", "e4m3", "f32"])
     ap.add_argument("--frames", type=int, default=256)
     ap.add_argument("--chain-len", type=int, default=10)
@@ -453,6 +549,8 @@ def main():
         raise SystemExit("--warmup must be >= 3")
     if args.impl == "reference":
         run_reference(args)
+    elif args.workload == "serve":
+        run_serve(args)
     else:
         run_ours(args)
 

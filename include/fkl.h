@@ -237,6 +237,124 @@ FKL_API fkl_status fkl_execute_batch_unfused_static(fkl_pipeline p, int32_t n, c
                                                     void* stream);
 
 /* ------------------------------------------------------------------------ */
+/* Host-buffer executor: overlapped copy-in, fused launch, copy-out          */
+/* ------------------------------------------------------------------------ */
+
+/*
+ * For callers whose images live in host memory. The executor owns `depth`
+ * device slots, each holding the inputs and outputs of up to `chunk` images
+ * (`in_bytes` and `out_bytes` per image at most), and three non-blocking
+ * streams (copy-in, compute, copy-out). fkl_execute_batch_host splits a
+ * batch into chunks and pipelines them: while chunk c is computed, chunk c+1
+ * is copied in and chunk c-1 copied out, so the host link in both directions
+ * and the fused kernel overlap. The paper measures device-resident data
+ * only; this is the library's data path from and to the host.
+ *
+ * create: allocates the slots (cudaMalloc) and streams on the current
+ * device; FKL_ERR_CUDA if that fails. destroy synchronises the executor's
+ * streams and frees everything.
+ * execute: `ins` are host tensors (HWC u8 or NV12, pinned memory for
+ * asynchronous copies; pageable memory works but serialises), `out` a host
+ * tensor laid out as for fkl_execute_batch. The call enqueues everything and
+ * returns; the work is ordered after earlier work on `stream`, and `stream`
+ * waits for its completion (synchronise `stream`, then read `out`). The host
+ * buffers must stay valid and unmodified until then. Images are copied into
+ * a slot at a 16-byte-aligned pitch, so vector loads apply to any host pitch.
+ * An image larger than `in_bytes` (or an output image larger than
+ * `out_bytes`) is FKL_ERR_INVALID. One fused launch per chunk.
+ */
+typedef struct fkl_host_executor_s* fkl_host_executor;
+FKL_API fkl_status fkl_host_executor_create(fkl_pipeline p, int32_t chunk, int32_t depth, size_t in_bytes,
+                                            size_t out_bytes, fkl_host_executor* out);
+FKL_API fkl_status fkl_execute_batch_host(fkl_host_executor e, int32_t n, const fkl_tensor* ins,
+                                          const int32_t* rois, fkl_tensor* out, void* stream);
+FKL_API void fkl_host_executor_destroy(fkl_host_executor e);
+
+/* ------------------------------------------------------------------------ */
+/* Serving: continuous batching of preprocessing requests                    */
+/* ------------------------------------------------------------------------ */
+
+/*
+ * A server runs one image chain (a READ_U8C3 [CROP] RESIZE ... WRITE_SPLIT
+ * pipeline) for a stream of requests, each a list of host images of mixed
+ * sizes. It is the horizontal fusion of paper §IV-B applied over time:
+ * requests that arrive while others run are admitted as soon as a request
+ * slot and enough device memory are free, and their images are processed
+ * alongside the ones already on the GPU. The paper has no serving loop; this
+ * is the library's.
+ *
+ * Modes:
+ *   FKL_SERVE_PERSISTENT  a persistent kernel (up to ctas_per_sm CTAs per SM)
+ *                         pulls image tasks from a queue in mapped host
+ *                         memory; every image of every admitted request is
+ *                         one task; request state lives on the device.
+ *   FKL_SERVE_BATCH       one fused fkl_execute_batch launch per request.
+ *   FKL_SERVE_UNFUSED     per request, the unfused one-kernel-per-op form
+ *                         (the conventional-library baseline).
+ * Admission: requests are admitted in arrival order (FIFO) when one of
+ * `max_inflight` slots is free and the first-fit allocator of a device arena
+ * of `arena_bytes` finds room for the request's images (copied with tight
+ * rows, one contiguous copy per image when the host rows are tight) and
+ * outputs. A request that could never fit is
+ * refused at submit (FKL_ERR_INVALID).
+ * Waits: the persistent kernel's CTAs stop after `idle_us` microseconds
+ * without work (or at destroy); the server relaunches them when work
+ * arrives. No device wait is unbounded.
+ * Threading: one internal host thread drives admission, copies, launches and
+ * completion; submit/poll/wait/release may be called from any thread.
+ * Times are CLOCK_MONOTONIC seconds.
+ */
+enum { FKL_SERVE_PERSISTENT = 0, FKL_SERVE_BATCH = 1, FKL_SERVE_UNFUSED = 2 };
+
+typedef struct {
+  int32_t mode;            /* FKL_SERVE_*                                      */
+  int32_t max_inflight;    /* request slots, 1..1024                           */
+  size_t arena_bytes;      /* device memory for admitted requests              */
+  int32_t ctas_per_sm;     /* persistent mode: CTAs per SM (1..8)              */
+  int32_t idle_us;         /* persistent mode: CTA idle timeout                */
+} fkl_server_config;
+
+typedef struct {
+  double t_submit;         /* submit() called                                  */
+  double t_admit;          /* slot and memory granted, copies enqueued         */
+  double t_ready;          /* copies to the device complete, work published    */
+  double t_done;           /* every output image written                       */
+  int32_t n_images;
+  int32_t state;           /* 0 queued, 1 copying, 2 running, 3 done           */
+} fkl_request_info;
+
+typedef struct {
+  uint64_t submitted, admitted, completed, images_completed;
+  uint64_t kernel_launches;     /* persistent kernels, or per-request launches */
+  uint64_t arena_peak_bytes;    /* high-water mark of the arena                */
+  int32_t queued, inflight;     /* right now                                   */
+} fkl_server_stats;
+
+typedef struct fkl_server_s* fkl_server;
+
+/* Create: allocates the arena and control blocks, starts the host thread.
+ * The pipeline must outlive the server. */
+FKL_API fkl_status fkl_server_create(fkl_pipeline p, const fkl_server_config* cfg, fkl_server* out);
+/* Submit n host images (HWC u8; pinned memory for asynchronous copies). The
+ * images must stay valid until the request's t_ready. Returns at once. */
+FKL_API fkl_status fkl_server_submit(fkl_server s, int32_t n, const fkl_tensor* images,
+                                     uint64_t* request_id);
+/* Non-blocking: *done = 1 once every output of the request is written;
+ * `out` (may be NULL) then describes the request's device output
+ * [n, 3, H, W] (valid until release). */
+FKL_API fkl_status fkl_server_poll(fkl_server s, uint64_t request_id, int32_t* done, fkl_tensor* out);
+/* Blocking poll with a timeout; FKL_ERR_TIMEOUT if not done in time. */
+FKL_API fkl_status fkl_server_wait(fkl_server s, uint64_t request_id, int32_t timeout_ms, fkl_tensor* out);
+/* Times and state of a request (before release). */
+FKL_API fkl_status fkl_server_request_info(fkl_server s, uint64_t request_id, fkl_request_info* info);
+/* Frees the request's slot and device memory (after it is done). */
+FKL_API fkl_status fkl_server_release(fkl_server s, uint64_t request_id);
+FKL_API fkl_status fkl_server_get_stats(fkl_server s, fkl_server_stats* st);
+/* Stops the host thread and the kernels, waits for in-flight work, frees
+ * everything. */
+FKL_API void fkl_server_destroy(fkl_server s);
+
+/* ------------------------------------------------------------------------ */
 /* Introspection and tuning                                                 */
 /* ------------------------------------------------------------------------ */
 
@@ -277,18 +395,18 @@ FKL_API fkl_status fkl_pipeline_shape_at(fkl_pipeline p, int32_t k,
  * launch, may be NULL) report it. Every trial writes `out`. Synchronises `stream`;
  * not capturable in a CUDA graph. A pipeline with a single shape returns it
  * without timing.
- * fkl_pipeline_autotune_flushed: the same, but before every timed launch it
- * overwrites `flush` (caller-owned device memory, `flush_bytes` bytes, best
- * larger than the L2 cache) with cudaMemsetAsync outside the timed interval,
- * so that inputs smaller than L2 are tuned from a cold cache.
+ * fkl_pipeline_autotune_ex: the same, but calls `before(user)` on the host
+ * before every timed launch, outside its timed interval, so the caller can
+ * enqueue the work that precedes a launch in its own steady state (for
+ * example an L2 flush, for inputs smaller than L2). `before` may be NULL.
  */
 FKL_API fkl_status fkl_pipeline_autotune(fkl_pipeline p, int32_t n, const fkl_tensor* ins,
                                          const int32_t* rois, fkl_tensor* out, void* stream,
                                          int32_t reps, fkl_launch_shape* best, float* best_us);
-FKL_API fkl_status fkl_pipeline_autotune_flushed(fkl_pipeline p, int32_t n, const fkl_tensor* ins,
-                                                 const int32_t* rois, fkl_tensor* out, void* stream,
-                                                 int32_t reps, void* flush, size_t flush_bytes,
-                                                 fkl_launch_shape* best, float* best_us);
+FKL_API fkl_status fkl_pipeline_autotune_ex(fkl_pipeline p, int32_t n, const fkl_tensor* ins,
+                                            const int32_t* rois, fkl_tensor* out, void* stream,
+                                            int32_t reps, void (*before)(void* user), void* user,
+                                            fkl_launch_shape* best, float* best_us);
 
 /* Library version string. */
 FKL_API const char* fkl_version(void);

@@ -11,12 +11,6 @@
 
 #include "registry.h"
 
-struct fkl_pipeline_s {
-  fkl_impl::Spec spec;
-  fkl_launch_shape shape;
-  std::string name;
-};
-
 namespace fkl_impl {
 
 namespace {
@@ -280,25 +274,10 @@ fkl_status image_params(const Spec& s, const fkl_tensor* t, const int32_t* roi_i
   r.ry = roi[1];
   r.rw = roi[2];
   r.rh = roi[3];
-  if (s.geom == GEOM_NONE) {
-    if (r.rw != od.W || r.rh != od.H)
-      return fail(FKL_ERR_INVALID, "input %d: ROI %dx%d must equal the %dx%d output when the chain has no resize", i,
-                  r.rw, r.rh, od.W, od.H);
-    r.dw = r.rw;
-    r.dh = r.rh;
-  } else if (s.geom == GEOM_RESIZE) {
-    r.dw = od.W;
-    r.dh = od.H;
-  } else {
-    const double sc = std::min(static_cast<double>(od.W) / r.rw, static_cast<double>(od.H) / r.rh);
-    r.dw = std::max(1, std::min(od.W, static_cast<int>(std::floor(r.rw * sc + 0.5))));
-    r.dh = std::max(1, std::min(od.H, static_cast<int>(std::floor(r.rh * sc + 0.5))));
-    r.ox = (od.W - r.dw) / 2;
-    r.oy = (od.H - r.dh) / 2;
-  }
-  r.pad = s.pad;
-  r.inv_area = static_cast<float>(1.0 / (4.0 * r.dw * r.dh));
-  if (r.rw == 2 * r.dw && r.rh == 2 * r.dh) r.flags |= fkl::kExact2x;
+  if (s.geom == GEOM_NONE && (r.rw != od.W || r.rh != od.H))
+    return fail(FKL_ERR_INVALID, "input %d: ROI %dx%d must equal the %dx%d output when the chain has no resize", i,
+                r.rw, r.rh, od.W, od.H);
+  place(s, od.W, od.H, r);
   if (s.family == FAM_NV12 && (r.flags & fkl::kExact2x) && r.rx % 16 == 0 && r.ry % 2 == 0 &&
       pitch % 16 == 0 && reinterpret_cast<uintptr_t>(r.src) % 16 == 0)
     r.flags |= fkl::kFast2x;
@@ -309,6 +288,27 @@ std::mutex g_sm_mu;
 int g_sm[64] = {0};
 
 }  // namespace
+
+void place(const Spec& s, int out_w, int out_h, fkl::ResampleParams& r) {
+  if (s.geom == GEOM_NONE) {
+    r.dw = r.rw;
+    r.dh = r.rh;
+  } else if (s.geom == GEOM_RESIZE) {
+    r.dw = out_w;
+    r.dh = out_h;
+  } else {
+    const double sc = std::min(static_cast<double>(out_w) / r.rw, static_cast<double>(out_h) / r.rh);
+    r.dw = std::max(1, std::min(out_w, static_cast<int>(std::floor(r.rw * sc + 0.5))));
+    r.dh = std::max(1, std::min(out_h, static_cast<int>(std::floor(r.rh * sc + 0.5))));
+    r.ox = (out_w - r.dw) / 2;
+    r.oy = (out_h - r.dh) / 2;
+  }
+  r.pad = s.pad;
+  r.inv_area = static_cast<float>(1.0 / (4.0 * r.dw * r.dh));
+  if (r.rw == 2 * r.dw && r.rh == 2 * r.dh) r.flags |= fkl::kExact2x;
+}
+
+void set_last_error(const char* msg) { t_error = msg; }
 
 int sm_count() {
   int dev = 0;
@@ -629,13 +629,12 @@ fkl_status fkl_pipeline_shape_at(fkl_pipeline p, int32_t k, fkl_launch_shape* sh
   return FKL_OK;
 }
 
-fkl_status fkl_pipeline_autotune_flushed(fkl_pipeline p, int32_t n, const fkl_tensor* ins, const int32_t* rois,
-                                         fkl_tensor* out, void* stream, int32_t reps, void* flush,
-                                         size_t flush_bytes, fkl_launch_shape* best, float* best_us) {
+fkl_status fkl_pipeline_autotune_ex(fkl_pipeline p, int32_t n, const fkl_tensor* ins, const int32_t* rois,
+                                    fkl_tensor* out, void* stream, int32_t reps, void (*before)(void*), void* user,
+                                    fkl_launch_shape* best, float* best_us) {
   constexpr int kMaxReps = 32;
   if (!p) return fail(FKL_ERR_INVALID, "null pipeline");
   if (reps < 1 || reps > kMaxReps) return fail(FKL_ERR_INVALID, "reps must be in 1..%d", kMaxReps);
-  if (flush_bytes && !flush) return fail(FKL_ERR_INVALID, "flush buffer missing");
   const bool vchain = p->spec.family == FAM_VCHAIN;
   auto run = [&]() -> fkl_status {
     return vchain ? fkl_execute(p, ins, out, stream) : fkl_execute_batch(p, n, ins, rois, out, stream);
@@ -658,7 +657,7 @@ fkl_status fkl_pipeline_autotune_flushed(fkl_pipeline p, int32_t n, const fkl_te
       p->shape = shapes[k];
       st = run();
       for (int r = 0; r < reps && st == FKL_OK && ce == cudaSuccess; ++r) {
-        if (flush_bytes && (ce = cudaMemsetAsync(flush, r & 0xFF, flush_bytes, s)) != cudaSuccess) break;
+        if (before) before(user);
         if ((ce = cudaEventRecord(ev[2 * r], s)) != cudaSuccess) break;
         st = run();
         if (st == FKL_OK) ce = cudaEventRecord(ev[2 * r + 1], s);
@@ -691,7 +690,7 @@ fkl_status fkl_pipeline_autotune_flushed(fkl_pipeline p, int32_t n, const fkl_te
 fkl_status fkl_pipeline_autotune(fkl_pipeline p, int32_t n, const fkl_tensor* ins, const int32_t* rois,
                                  fkl_tensor* out, void* stream, int32_t reps, fkl_launch_shape* best,
                                  float* best_us) {
-  return fkl_pipeline_autotune_flushed(p, n, ins, rois, out, stream, reps, nullptr, 0, best, best_us);
+  return fkl_pipeline_autotune_ex(p, n, ins, rois, out, stream, reps, nullptr, nullptr, best, best_us);
 }
 
 fkl_status fkl_execute_batch_unfused_static(fkl_pipeline p, int32_t n, const fkl_tensor* ins, const int32_t* rois,

@@ -110,11 +110,25 @@ FKL_D F3 blend_float(const F3& t00, const F3& t01, const F3& t10, const F3& t11,
 // Read Operations
 // ===========================================================================
 
+// Source loads: through the read-only (non-coherent) path by default, or
+// L2-only (`ld.global.cg`) for kernels whose source memory is rewritten while
+// they run (the persistent serving kernel reuses its device arena), where a
+// stale L1 line must never be read.
+template <bool kCoherent>
+FKL_D uint8_t load_u8(const uint8_t* p) {
+  if constexpr (kCoherent) {
+    return __ldcg(p);
+  } else {
+    return __ldg(p);
+  }
+}
+
 // Packed 3-channel u8 image, crop window, bilinear resize and placement.
 // The four taps are u8 integers, so the blend is done exactly in integers:
 // N = (Dy - wy)((Dx - wx) S00 + wx S01) + wy((Dx - wx) S10 + wx S11) and the
 // value is N / (Dx Dy) with a single float conversion and one multiply.
-struct ResizeU8C3 {
+template <bool kCoherent>
+struct ResizeU8C3T {
   using InstanceType = ReadType;
   using ParamsType = ResampleParams;
   using OutputType = F3;
@@ -132,8 +146,8 @@ struct ResizeU8C3 {
     F3 o;
 #pragma unroll
     for (int c = 0; c < 3; ++c) {
-      const uint32_t top = wx0 * __ldg(p00 + c) + wx1 * __ldg(p01 + c);
-      const uint32_t bot = wx0 * __ldg(p10 + c) + wx1 * __ldg(p11 + c);
+      const uint32_t top = wx0 * load_u8<kCoherent>(p00 + c) + wx1 * load_u8<kCoherent>(p01 + c);
+      const uint32_t bot = wx0 * load_u8<kCoherent>(p10 + c) + wx1 * load_u8<kCoherent>(p11 + c);
       const uint64_t n = static_cast<uint64_t>(wy0) * top + static_cast<uint64_t>(wy1) * bot;
       o.v[c] = __fmul_rn(__ull2float_rn(n), inv_area);
     }
@@ -173,6 +187,8 @@ struct ResizeU8C3 {
     }
   }
 };
+
+using ResizeU8C3 = ResizeU8C3T<false>;
 
 // BT.601 limited-range decode constants, divided by 255 so that the clamp to
 // [0, 255] becomes the free [0, 1] saturation of an add:

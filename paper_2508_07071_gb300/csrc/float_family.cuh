@@ -59,9 +59,18 @@ auto make_tail(const Spec& s) {
   }
 }
 
-template <class ROp, class OutT, bool kSplit, bool kSwap, int kTail, int V, int RY>
-cudaError_t run_float_chain(const LaunchCtx& c) {
-  using RB = fkl::BatchRead<ROp, kBatchCap>;
+// Batches of up to kSmallCap images use a small parameter block (a launch
+// carries its whole parameter block, 16 KB for kBatchCap entries), for ROps
+// that serve single images.
+constexpr int kSmallCap = 8;
+template <class ROp>
+struct SmallBatches : std::false_type {};
+template <>
+struct SmallBatches<fkl::ResizeU8C3> : std::true_type {};
+
+template <class ROp, class OutT, bool kSplit, bool kSwap, int kTail, int V, int RY, int CAP>
+cudaError_t run_float_chain_cap(const LaunchCtx& c) {
+  using RB = fkl::BatchRead<ROp, CAP>;
   using W = std::conditional_t<kSplit, fkl::WriteSplit<OutT>, fkl::WritePacked<OutT>>;
   const Spec& s = *c.spec;
   auto tail = make_tail<kTail>(s);
@@ -82,6 +91,14 @@ cudaError_t run_float_chain(const LaunchCtx& c) {
   a.H = c.H;
   a.W_ = c.W;
   return fkl::launch_transform2d<V, RY>(a, c.n, c.shape.tx, c.shape.ty, c.stream);
+}
+
+template <class ROp, class OutT, bool kSplit, bool kSwap, int kTail, int V, int RY>
+cudaError_t run_float_chain(const LaunchCtx& c) {
+  if constexpr (SmallBatches<ROp>::value) {
+    if (c.n <= kSmallCap) return run_float_chain_cap<ROp, OutT, kSplit, kSwap, kTail, V, RY, kSmallCap>(c);
+  }
+  return run_float_chain_cap<ROp, OutT, kSplit, kSwap, kTail, V, RY, kBatchCap>(c);
 }
 
 template <class ROp, class OutT, bool kSplit, bool kSwap, int kTail, int V>

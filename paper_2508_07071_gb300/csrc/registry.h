@@ -3,6 +3,7 @@
 #pragma once
 
 #include <cstdint>
+#include <string>
 #include <vector>
 
 #include "../../include/fkl.h"
@@ -80,4 +81,18 @@ fkl_launch_shape default_shape(const Spec& s);
 
 int sm_count();
 
+// Sets the thread-local message returned by fkl_last_error().
+void set_last_error(const char* msg);
+
+// Resize / letterbox placement of a source window (r.rx..r.rh set) in an
+// out_w x out_h output: fills dw, dh, ox, oy, pad, inv_area, kExact2x.
+void place(const Spec& s, int out_w, int out_h, fkl::ResampleParams& r);
+
 }  // namespace fkl_impl
+
+// A bound chain (the handle behind fkl_pipeline).
+struct fkl_pipeline_s {
+  fkl_impl::Spec spec;
+  fkl_launch_shape shape;
+  std::string name;
+};

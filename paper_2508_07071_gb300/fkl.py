@@ -58,6 +58,25 @@ class fkl_launch_shape(ctypes.Structure):
         return (self.vec, self.tx, self.ty, self.ry)
 
 
+FKL_SERVE_PERSISTENT, FKL_SERVE_BATCH, FKL_SERVE_UNFUSED = range(3)
+
+
+class fkl_server_config(ctypes.Structure):
+    _fields_ = [("mode", ctypes.c_int32), ("max_inflight", ctypes.c_int32), ("arena_bytes", ctypes.c_size_t),
+                ("ctas_per_sm", ctypes.c_int32), ("idle_us", ctypes.c_int32)]
+
+
+class fkl_request_info(ctypes.Structure):
+    _fields_ = [("t_submit", ctypes.c_double), ("t_admit", ctypes.c_double), ("t_ready", ctypes.c_double),
+                ("t_done", ctypes.c_double), ("n_images", ctypes.c_int32), ("state", ctypes.c_int32)]
+
+
+class fkl_server_stats(ctypes.Structure):
+    _fields_ = [("submitted", ctypes.c_uint64), ("admitted", ctypes.c_uint64), ("completed", ctypes.c_uint64),
+                ("images_completed", ctypes.c_uint64), ("kernel_launches", ctypes.c_uint64),
+                ("arena_peak_bytes", ctypes.c_uint64), ("queued", ctypes.c_int32), ("inflight", ctypes.c_int32)]
+
+
 class FklError(RuntimeError):
     def __init__(self, status: int, message: str):
         super().__init__(f"fkl status {status}: {message}")
@@ -100,13 +119,33 @@ EXPORTS = {
                                              ctypes.c_void_p, ctypes.c_int32,
                                              ctypes.POINTER(fkl_launch_shape),
                                              ctypes.POINTER(ctypes.c_float)]),
-    "fkl_pipeline_autotune_flushed": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int32,
-                                                     ctypes.POINTER(fkl_tensor),
-                                                     ctypes.POINTER(ctypes.c_int32),
-                                                     ctypes.POINTER(fkl_tensor), ctypes.c_void_p,
-                                                     ctypes.c_int32, ctypes.c_void_p, ctypes.c_size_t,
-                                                     ctypes.POINTER(fkl_launch_shape),
-                                                     ctypes.POINTER(ctypes.c_float)]),
+    "fkl_pipeline_autotune_ex": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int32,
+                                                ctypes.POINTER(fkl_tensor),
+                                                ctypes.POINTER(ctypes.c_int32),
+                                                ctypes.POINTER(fkl_tensor), ctypes.c_void_p,
+                                                ctypes.c_int32, ctypes.c_void_p, ctypes.c_void_p,
+                                                ctypes.POINTER(fkl_launch_shape),
+                                                ctypes.POINTER(ctypes.c_float)]),
+    "fkl_host_executor_create": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int32, ctypes.c_int32,
+                                                ctypes.c_size_t, ctypes.c_size_t,
+                                                ctypes.POINTER(ctypes.c_void_p)]),
+    "fkl_execute_batch_host": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int32, ctypes.POINTER(fkl_tensor),
+                                              ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(fkl_tensor),
+                                              ctypes.c_void_p]),
+    "fkl_host_executor_destroy": (None, [ctypes.c_void_p]),
+    "fkl_server_create": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(fkl_server_config),
+                                         ctypes.POINTER(ctypes.c_void_p)]),
+    "fkl_server_submit": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int32, ctypes.POINTER(fkl_tensor),
+                                         ctypes.POINTER(ctypes.c_uint64)]),
+    "fkl_server_poll": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_uint64, ctypes.POINTER(ctypes.c_int32),
+                                       ctypes.POINTER(fkl_tensor)]),
+    "fkl_server_wait": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_uint64, ctypes.c_int32,
+                                       ctypes.POINTER(fkl_tensor)]),
+    "fkl_server_request_info": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_uint64,
+                                               ctypes.POINTER(fkl_request_info)]),
+    "fkl_server_release": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_uint64]),
+    "fkl_server_get_stats": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(fkl_server_stats)]),
+    "fkl_server_destroy": (None, [ctypes.c_void_p]),
     "fkl_version": (ctypes.c_char_p, []),
 }
 
@@ -405,22 +444,92 @@ def fkl_pipeline_shapes(p: int) -> list:
     return out
 
 
+_BEFORE = ctypes.CFUNCTYPE(None, ctypes.c_void_p)
+
+
 def fkl_pipeline_autotune(p: int, ins: Sequence[fkl_tensor], rois, out: fkl_tensor, stream=None,
-                          reps: int = 5, flush_ptr: int = 0, flush_bytes: int = 0):
-    """Returns (best shape, median microseconds per launch). With a flush
-    buffer, every timed launch starts from a cold L2."""
+                          reps: int = 5, before=None):
+    """Returns (best shape, median microseconds per launch). `before()` (a
+    Python callable) runs before every timed launch, e.g. an L2 flush."""
     arr = (fkl_tensor * max(1, len(ins)))(*ins)
     keep = _rois(rois)
     best = fkl_launch_shape()
     us = ctypes.c_float()
-    if flush_bytes:
-        _check(_lib.fkl_pipeline_autotune_flushed(p, len(ins), arr, keep[1] if keep else None,
-                                                  ctypes.byref(out), _stream(stream), reps, flush_ptr,
-                                                  flush_bytes, ctypes.byref(best), ctypes.byref(us)))
+    if before is not None:
+        cb = _BEFORE(lambda _user: before())
+        _check(_lib.fkl_pipeline_autotune_ex(p, len(ins), arr, keep[1] if keep else None,
+                                             ctypes.byref(out), _stream(stream), reps,
+                                             ctypes.cast(cb, ctypes.c_void_p), None,
+                                             ctypes.byref(best), ctypes.byref(us)))
     else:
         _check(_lib.fkl_pipeline_autotune(p, len(ins), arr, keep[1] if keep else None, ctypes.byref(out),
                                           _stream(stream), reps, ctypes.byref(best), ctypes.byref(us)))
     return best.as_tuple(), us.value
+
+
+def fkl_host_executor_create(p: int, chunk: int, depth: int, in_bytes: int, out_bytes: int) -> int:
+    h = ctypes.c_void_p()
+    _check(_lib.fkl_host_executor_create(p, chunk, depth, in_bytes, out_bytes, ctypes.byref(h)))
+    return h.value
+
+
+def fkl_host_executor_destroy(e: int) -> None:
+    _lib.fkl_host_executor_destroy(e)
+
+
+def fkl_execute_batch_host(e: int, ins: Sequence[fkl_tensor], rois, out: fkl_tensor, stream=None) -> None:
+    arr = (fkl_tensor * max(1, len(ins)))(*ins)
+    keep = _rois(rois)
+    _check(_lib.fkl_execute_batch_host(e, len(ins), arr, keep[1] if keep else None, ctypes.byref(out),
+                                       _stream(stream)))
+
+
+def fkl_server_create(p: int, mode: int = FKL_SERVE_PERSISTENT, max_inflight: int = 64,
+                      arena_bytes: int = 4 << 30, ctas_per_sm: int = 4, idle_us: int = 200000) -> int:
+    cfg = fkl_server_config(mode, max_inflight, arena_bytes, ctas_per_sm, idle_us)
+    h = ctypes.c_void_p()
+    _check(_lib.fkl_server_create(p, ctypes.byref(cfg), ctypes.byref(h)))
+    return h.value
+
+
+def fkl_server_submit(s: int, images: Sequence[fkl_tensor]) -> int:
+    arr = (fkl_tensor * len(images))(*images)
+    rid = ctypes.c_uint64()
+    _check(_lib.fkl_server_submit(s, len(images), arr, ctypes.byref(rid)))
+    return rid.value
+
+
+def fkl_server_poll(s: int, rid: int):
+    done = ctypes.c_int32()
+    out = fkl_tensor()
+    _check(_lib.fkl_server_poll(s, rid, ctypes.byref(done), ctypes.byref(out)))
+    return bool(done.value), out
+
+
+def fkl_server_wait(s: int, rid: int, timeout_ms: int = 10000) -> fkl_tensor:
+    out = fkl_tensor()
+    _check(_lib.fkl_server_wait(s, rid, timeout_ms, ctypes.byref(out)))
+    return out
+
+
+def fkl_server_request_info(s: int, rid: int) -> fkl_request_info:
+    info = fkl_request_info()
+    _check(_lib.fkl_server_request_info(s, rid, ctypes.byref(info)))
+    return info
+
+
+def fkl_server_release(s: int, rid: int) -> None:
+    _check(_lib.fkl_server_release(s, rid))
+
+
+def fkl_server_get_stats(s: int) -> fkl_server_stats:
+    st = fkl_server_stats()
+    _check(_lib.fkl_server_get_stats(s, ctypes.byref(st)))
+    return st
+
+
+def fkl_server_destroy(s: int) -> None:
+    _lib.fkl_server_destroy(s)
 
 
 class Pipeline:

@@ -73,3 +73,22 @@ def check_output(out: torch.Tensor, want: np.ndarray, fmt: str, scale: float = 1
     if fmt == "f32":
         return check_f32(to_numpy(out), want, what)
     return check_lowp(to_numpy(out), want, fmt, scale, what)
+
+
+_cudart = None
+
+
+def copy_device(ptr: int, nbytes: int) -> torch.Tensor:
+    """Copy `nbytes` of device memory at a raw pointer into a new uint8
+    tensor on the GPU (for outputs the library hands back as pointers)."""
+    import ctypes
+    global _cudart
+    if _cudart is None:
+        _cudart = ctypes.CDLL("libcudart.so.13")
+        _cudart.cudaMemcpy.argtypes = [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_size_t, ctypes.c_int]
+        _cudart.cudaMemcpy.restype = ctypes.c_int
+    out = torch.empty(nbytes, dtype=torch.uint8, device="cuda")
+    torch.cuda.synchronize()
+    rc = _cudart.cudaMemcpy(out.data_ptr(), ptr, nbytes, 3)  # device to device
+    assert rc == 0, f"cudaMemcpy failed with {rc}"
+    return out

@@ -410,3 +410,34 @@ def test_autotune_keeps_results(F, W):
     y = torch.empty_like(x)
     best, us = F.fkl_pipeline_autotune(pv.handle, [F.as_fkl(x)], None, F.as_fkl(y), reps=2)
     assert best in F.fkl_pipeline_shapes(pv.handle)
+
+
+def test_host_executor_matches_device_path(F, W):
+    n = 37                                            # 5 chunks of 8, ragged last chunk
+    frames = synth.nv12_frames(13, n, 720, 1280)
+    host_in = torch.from_numpy(frames).pin_memory()
+    host_out = torch.zeros((n, 3, 640, 640), dtype=torch.bfloat16).pin_memory()
+    p = F.Pipeline(W.nv12_letterbox_chain(F.FKL_BF16))
+    e = F.fkl_host_executor_create(p.handle, 8, 3, 1080 * 1280, 3 * 640 * 640 * 2)
+    try:
+        ins = [F.as_fkl(host_in[i], F.FKL_LAYOUT_NV12) for i in range(n)]
+        for _ in range(2):                            # slots are reused across calls
+            host_out.zero_()
+            F.fkl_execute_batch_host(e, ins, None, F.as_fkl(host_out, F.FKL_LAYOUT_NCHW))
+            torch.cuda.synchronize()
+            ref, _ = nv12_case(F, W, "bf16", frames)
+            assert torch.equal(host_out.view(torch.uint8), ref.cpu().view(torch.uint8))
+        # pitched host images (copied with 2-D copies) and an image too big for a slot
+        big = torch.zeros((n, 1080, 1296), dtype=torch.uint8).pin_memory()
+        big[:, :, :1280] = host_in
+        ins2 = [F.as_fkl(big[i, :, :1280], F.FKL_LAYOUT_NV12) for i in range(4)]
+        out2 = torch.zeros((4, 3, 640, 640), dtype=torch.bfloat16).pin_memory()
+        F.fkl_execute_batch_host(e, ins2, None, F.as_fkl(out2, F.FKL_LAYOUT_NCHW))
+        torch.cuda.synchronize()
+        assert torch.equal(out2.view(torch.uint8), host_out[:4].view(torch.uint8))
+        huge = torch.zeros((2160 * 3 // 2, 3840), dtype=torch.uint8)
+        with pytest.raises(F.FklError):
+            F.fkl_execute_batch_host(e, [F.as_fkl(huge, F.FKL_LAYOUT_NV12)], None,
+                                     F.as_fkl(out2, F.FKL_LAYOUT_NCHW))
+    finally:
+        F.fkl_host_executor_destroy(e)
