@@ -327,11 +327,19 @@ def run_ours(args):
 
         # unfused chain on the same GPU (a few steps)
         ku = min(args.steps, args.unfused_steps)
-        unfused_ms = None
+        unfused_ms = graph_ms = None
         if ku > 0:
             wl.step_unfused(stream)
             torch.cuda.synchronize()
             unfused_ms = float(np.mean(time_steps(torch, wl.step_unfused, ku, stream, between)))
+            # the same per-op launches captured once in a CUDA graph and replayed
+            # (the paper's CUDA-Graphs comparison: one node per kernel)
+            graph = torch.cuda.CUDAGraph()
+            with torch.cuda.graph(graph, stream=stream):
+                wl.step_unfused(stream)
+            graph.replay()
+            torch.cuda.synchronize()
+            graph_ms = float(np.mean(time_steps(torch, lambda st: graph.replay(), ku, stream, between)))
 
         # end to end through the public call with host buffers
         ke = min(args.steps, args.e2e_steps)
@@ -373,7 +381,8 @@ def run_ours(args):
         "unfused": None if unfused_ms is None else {
             "ms_per_step": round(unfused_ms, 4), "speedup": round(unfused_ms / ms_per_step, 2),
             "traffic_ratio": round(wl.unfused_bytes() / wl.bytes, 2), "steps": ku,
-            "launches_per_step": getattr(wl, "unfused_launches", None)},
+            "cuda_graph_ms_per_step": round(graph_ms, 4),
+            "speedup_vs_cuda_graph": round(graph_ms / ms_per_step, 2)},
         "roofline": {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
                      "frac": round(achieved / peak, 4), "traffic": None,
                      "peak_source": f"{peak_kind} copy bandwidth (MEASURED_PEAKS.json hbm_gbs)"
@@ -481,6 +490,82 @@ def run_serve(args):
           flush=True)
 
 
+def run_sweeps(args):
+    """The paper's parameter sweeps on GB300, fused vs unfused per point:
+    Exp 4 (§VI-D) VF+HF: 50 images of 60x120 u8, 1..10,000 Mul+Add pairs;
+    Exp 7 (§VI-G) data size: 100 .. 16,654,030 floats, 100 Mul+Add pairs;
+    Exp 5 (§VI-E) instructions per op: 500 Mul/Add instructions on
+    3840*2160*8 floats split into N kernels of M = 500/N ops each."""
+    import torch
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_2508_07071_gb300 import fkl as F, synth, workloads as W
+
+    stream = torch.cuda.Stream()
+    res = {"exp4_vf_hf": [], "exp7_data_size": [], "exp5_ops_per_kernel": []}
+
+    def t(fn, k):
+        fn(stream)
+        torch.cuda.synchronize()
+        return float(np.median(time_steps(torch, fn, k, stream)))
+
+    with torch.cuda.stream(stream):
+        # Exp 4: VF + HF, u8 input, batch 50 x 60 x 120 (one launch for the batch)
+        n = 50 * 60 * 120
+        x = torch.from_numpy(synth.packed_image(40, 1, n, 1).reshape(-1)).cuda()
+        y = torch.empty(n, device="cuda")
+        for pairs in [1, 10, 100, 1000, 5000, 10000]:
+            kinds, consts = synth.chain_constants(40, 2 * pairs)
+            p = F.Pipeline(W.vertical_chain(kinds, consts, u8_input=True))
+            F.fkl_pipeline_autotune(p.handle, [F.as_fkl(x)], None, F.as_fkl(y), stream=stream, reps=5)
+            fused = t(lambda st: F.fkl_execute(p.handle, F.as_fkl(x), F.as_fkl(y), stream=st), 10)
+            k_unf = 3 if pairs <= 1000 else 1
+            unf = t(lambda st: F.fkl_execute_batch_unfused(p.handle, [F.as_fkl(x)], None, F.as_fkl(y), 0, 0,
+                                                           stream=st), k_unf)
+            ops = n * 2 * pairs
+            res["exp4_vf_hf"].append({"pairs": pairs, "fused_ms": round(fused, 4), "unfused_ms": round(unf, 3),
+                                      "speedup": round(unf / fused, 1),
+                                      "fused_Gops_per_s": round(ops / fused / 1e6, 1)})
+            print(json.dumps({"exp4": res["exp4_vf_hf"][-1]}), flush=True)
+        # Exp 7: data size, 100 Mul+Add pairs, float32
+        kinds, consts = synth.chain_constants(41, 200)
+        p = F.Pipeline(W.vertical_chain(kinds, consts))
+        for n in [100, 10_000, 282_370, 1_000_000, 9_032_740, 16_654_030]:
+            x = torch.from_numpy(synth.f32_uniform(41, n)).cuda()
+            y = torch.empty_like(x)
+            F.fkl_pipeline_autotune(p.handle, [F.as_fkl(x)], None, F.as_fkl(y), stream=stream, reps=5)
+            fused = t(lambda st: F.fkl_execute(p.handle, F.as_fkl(x), F.as_fkl(y), stream=st), 20)
+            unf = t(lambda st: F.fkl_execute_batch_unfused(p.handle, [F.as_fkl(x)], None, F.as_fkl(y), 0, 0,
+                                                           stream=st), 5)
+            res["exp7_data_size"].append({"elements": n, "fused_ms": round(fused, 4), "unfused_ms": round(unf, 3),
+                                          "speedup": round(unf / fused, 1),
+                                          "fused_GBps": round(8 * n / fused / 1e6, 1)})
+            print(json.dumps({"exp7": res["exp7_data_size"][-1]}), flush=True)
+        # Exp 5: 500 instructions split into N kernels of M ops (M * N = 500)
+        n = 3840 * 2160 * 8
+        x = torch.from_numpy(synth.f32_uniform(42, n)).cuda()
+        y = torch.empty_like(x)
+        kinds, consts = synth.chain_constants(42, 500)
+        full = F.Pipeline(W.vertical_chain(kinds, consts))
+        F.fkl_pipeline_autotune(full.handle, [F.as_fkl(x)], None, F.as_fkl(y), stream=stream, reps=3)
+        fused = t(lambda st: F.fkl_execute(full.handle, F.as_fkl(x), F.as_fkl(y), stream=st), 5)
+        for m in [1, 5, 25, 100, 250, 500]:
+            parts = [F.Pipeline(W.vertical_chain(kinds[i:i + m], consts[i:i + m])) for i in range(0, 500, m)]
+            for q in parts:
+                F.fkl_pipeline_set_shape(q.handle, F.fkl_pipeline_get_shape(full.handle))
+
+            def chain(st):
+                F.fkl_execute(parts[0].handle, F.as_fkl(x), F.as_fkl(y), stream=st)
+                for q in parts[1:]:
+                    F.fkl_execute(q.handle, F.as_fkl(y), F.as_fkl(y), stream=st)
+            split = t(chain, 3)
+            res["exp5_ops_per_kernel"].append({"ops_per_kernel": m, "kernels": len(parts),
+                                               "split_ms": round(split, 3), "fused_500_ms": round(fused, 3),
+                                               "speedup": round(split / fused, 2)})
+            print(json.dumps({"exp5": res["exp5_ops_per_kernel"][-1]}), flush=True)
+    print(json.dumps({"metric": "paper sweeps (Exp 4, 5, 7) on GB300", "results": res}), flush=True)
+
+
 def run_reference(args):
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
@@ -528,7 +613,7 @@ def main():
     ap.add_argument("--steps", type=int, default=200)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="nv12", choices=["nv12", "single", "hf", "vchain", "serve"])
+    ap.add_argument("--workload", default="nv12", choices=["nv12", "single", "hf", "vchain", "serve", "sweeps"])
     ap.add_argument("--rates", default="200,500,1000,2000", help="serve: request rates (req/s)")
     ap.add_argument("--requests", type=int, default=200, help="serve: requests per rate")
     ap.add_argument("--pool", type=int, default=48, help="serve: distinct host images")
@@ -551,6 +636,8 @@ def main():
         run_reference(args)
     elif args.workload == "serve":
         run_serve(args)
+    elif args.workload == "sweeps":
+        run_sweeps(args)
     else:
         run_ours(args)
 

@@ -90,6 +90,8 @@ enum {
   FKL_OP_READ_U8C3 = 1,  /* packed 3-channel u8 image (HWC)                 */
   FKL_OP_READ_NV12 = 2,  /* NV12 frame, decoded BT.601 limited range to RGB */
   FKL_OP_READ_F32 = 3,   /* linear float32 tensor                           */
+  FKL_OP_READ_U8 = 4,    /* linear u8 tensor, converted to float exactly
+                            (vertical chains)                              */
 
   /* Read modifiers: together with the source they form the one ROp.       */
   FKL_OP_CROP = 10,      /* i[0..3] = x, y, w, h of the window read        */
@@ -140,7 +142,7 @@ typedef struct fkl_pipeline_s* fkl_pipeline;  /* library-owned handle        */
  *        (float math; output F32/F16/BF16/E4M3)
  *   READ_NV12 (RESIZE|LETTERBOX) [SWAP_RB] [MUL] [ADD|SUB] [DIV] WRITE_{SPLIT,PACKED}
  *   READ_U8C3 [CROP] [SWAP_RB] [ADD_SAT_U8] WRITE_{SPLIT,PACKED} (U8 output)
- *   READ_F32 (MUL|ADD){0..65536} WRITE_PACKED(F32)   (vertical chain)
+ *   READ_F32|READ_U8 (MUL|ADD){0..65536} WRITE_PACKED(F32)   (vertical chain)
  * An absent MUL/ADD/SUB/DIV is bound as its identity (x*1, x-0, x/1 are
  * exact, so the result equals the shorter chain bit for bit). A chain of the
  * right grammar outside this set returns FKL_ERR_UNSUPPORTED.
@@ -156,8 +158,8 @@ FKL_API fkl_status fkl_pipeline_create(const fkl_op_desc* ops, int32_t n_ops,
  * CROP descriptor's, else the whole image. `out` is NCHW (WRITE_SPLIT) or
  * NHWC (WRITE_PACKED) with N = 1 and the dtype the WOp names; its H, W must
  * equal the RESIZE/LETTERBOX size (the ROI size when there is no resize).
- * Vertical chains: `in` and `out` are LINEAR F32 of the same length (may
- * alias). stream is a cudaStream_t. One kernel launch per call (vertical
+ * Vertical chains: `in` (LINEAR F32, or U8 for READ_U8) and `out` (LINEAR
+ * F32) have the same length (F32 input may alias the output). stream is a cudaStream_t. One kernel launch per call (vertical
  * chains longer than 4096 ops use one launch per 4096 ops).
  */
 FKL_API fkl_status fkl_execute(fkl_pipeline p, const fkl_tensor* in, fkl_tensor* out,
@@ -235,6 +237,41 @@ FKL_API fkl_status fkl_execute_batch_unfused(fkl_pipeline p, int32_t n,
 FKL_API fkl_status fkl_execute_batch_unfused_static(fkl_pipeline p, int32_t n, const fkl_tensor* ins,
                                                     const int32_t* rois, fkl_tensor* out,
                                                     void* stream);
+
+/* ------------------------------------------------------------------------ */
+/* ReduceDPP: several reductions from one read; dynamic FP8 scaling         */
+/* ------------------------------------------------------------------------ */
+
+/*
+ * The reduction pattern of paper §IV-C: the pipeline's ROp and COps are
+ * evaluated once per output pixel of an fkl_execute_batch call with these
+ * arguments, and instead of the WOp the values feed several reductions at
+ * once. `out` fixes the output size and is not written. `stats` is device
+ * memory of FKL_REDUCE_STATS_BYTES bytes, 16-byte aligned; when the work is
+ * done (stream order) it holds floats:
+ *   [0..2] minimum per channel   [3..5] maximum per channel
+ *   [6..8] mean per channel      [9]    maximum absolute value, amax
+ *   [10]   s = amax / 448, the per-tensor scale that maps the values onto
+ *          the FP8-E4M3 range (1 when amax is 0)   [11] 1 / s
+ * Bytes 64..127 are the accumulator (overwritten). Float image families
+ * only (READ_U8C3 / READ_NV12 with a resize or letterbox). Launches: two
+ * memsets, one reduction launch per 256 images and one finishing kernel.
+ * Min/max are exact; the mean is accumulated in 64-bit fixed point
+ * (2^-20), independent of the order in which blocks finish.
+ */
+#define FKL_REDUCE_STATS_BYTES 128
+FKL_API fkl_status fkl_reduce_batch(fkl_pipeline p, int32_t n, const fkl_tensor* ins, const int32_t* rois,
+                                    const fkl_tensor* out, float* stats, void* stream);
+
+/*
+ * fkl_execute_batch with the FP8-E4M3 scale read from device memory:
+ * `scale_inv_dev` points at 1/s (e.g. stats + 11 of fkl_reduce_batch), so a
+ * reduce pass and a write pass give dynamic per-tensor scaling with no
+ * host round trip. The pipeline's WOp must write E4M3.
+ */
+FKL_API fkl_status fkl_execute_batch_scaled(fkl_pipeline p, int32_t n, const fkl_tensor* ins,
+                                            const int32_t* rois, fkl_tensor* out, const float* scale_inv_dev,
+                                            void* stream);
 
 /* ------------------------------------------------------------------------ */
 /* Host-buffer executor: overlapped copy-in, fused launch, copy-out          */

@@ -354,3 +354,21 @@ def integer_chain_packed(src: np.ndarray, roi, swap: bool, add_k) -> np.ndarray:
     if swap:
         t = swap_rb(t)
     return add_saturate_u8(t, add_k)
+
+
+# ----------------------------------------------------------------------------
+# Reductions of a chain's values (the reduction pattern of §IV-C)
+# ----------------------------------------------------------------------------
+
+
+def reduce_stats(values: np.ndarray) -> dict:
+    """Per-channel min, max and mean of planar values [N, C, H, W] (or
+    [C, H, W]), the maximum absolute value over everything, and the E4M3
+    per-tensor scale amax / 448 (1 when amax is 0)."""
+    v = np.asarray(values, dtype=np.float64)
+    if v.ndim == 3:
+        v = v[None]
+    per_c = np.moveaxis(v, 1, 0).reshape(v.shape[1], -1)
+    amax = float(np.max(np.abs(v)))
+    return {"min": per_c.min(axis=1), "max": per_c.max(axis=1), "mean": per_c.mean(axis=1),
+            "amax": amax, "scale": amax / E4M3_MAX if amax > 0 else 1.0}

@@ -65,7 +65,9 @@ const char* dtype_name(int dt) {
   }
 }
 
-bool is_read(int op) { return op == FKL_OP_READ_U8C3 || op == FKL_OP_READ_NV12 || op == FKL_OP_READ_F32; }
+bool is_read(int op) {
+  return op == FKL_OP_READ_U8C3 || op == FKL_OP_READ_NV12 || op == FKL_OP_READ_F32 || op == FKL_OP_READ_U8;
+}
 bool is_write(int op) { return op == FKL_OP_WRITE_PACKED || op == FKL_OP_WRITE_SPLIT; }
 bool is_modifier(int op) { return op == FKL_OP_CROP || op == FKL_OP_RESIZE || op == FKL_OP_LETTERBOX; }
 bool is_compute(int op) {
@@ -97,8 +99,9 @@ fkl_status parse(const fkl_op_desc* ops, int n, Spec& s) {
     s.fp8_scale = sc;
   }
 
-  if (src == FKL_OP_READ_F32) {
+  if (src == FKL_OP_READ_F32 || src == FKL_OP_READ_U8) {
     s.family = FAM_VCHAIN;
+    s.vinput_u8 = src == FKL_OP_READ_U8;
     for (int k = 1; k < n - 1; ++k) {
       const int op = ops[k].op;
       if (op == FKL_OP_MUL || op == FKL_OP_ADD) {
@@ -412,6 +415,7 @@ std::string make_name(const Spec& s) {
       break;
   }
   if (s.family == FAM_VCHAIN) {
+    if (s.vinput_u8) n = "fused:ReadU8";
     n += ">(Mul|Add)x" + std::to_string(s.vkinds.size()) + ">WriteF32";
     return n;
   }
@@ -445,11 +449,13 @@ cudaError_t launch_family(const LaunchCtx& c) {
   }
 }
 
-fkl_status check_linear(const fkl_tensor* in, const fkl_tensor* out, int64_t& n) {
+fkl_status check_linear(const Spec& s, const fkl_tensor* in, const fkl_tensor* out, int64_t& n) {
   if (!in || !out || !in->data || !out->data) return fail(FKL_ERR_INVALID, "tensor missing");
-  if (in->layout != FKL_LAYOUT_LINEAR || out->layout != FKL_LAYOUT_LINEAR || in->dtype != FKL_F32 ||
+  const int in_dt = s.vinput_u8 ? FKL_U8 : FKL_F32;
+  if (in->layout != FKL_LAYOUT_LINEAR || out->layout != FKL_LAYOUT_LINEAR || in->dtype != in_dt ||
       out->dtype != FKL_F32)
-    return fail(FKL_ERR_INVALID, "float32 tensor chains need LINEAR F32 input and output");
+    return fail(FKL_ERR_INVALID, "tensor chains need a LINEAR %s input and a LINEAR F32 output",
+                s.vinput_u8 ? "U8" : "F32");
   if (in->dims[0] != out->dims[0] || in->dims[0] < 0)
     return fail(FKL_ERR_INVALID, "input and output lengths differ (%lld vs %lld)", (long long)in->dims[0],
                 (long long)out->dims[0]);
@@ -473,6 +479,37 @@ fkl_status validate_batch(const fkl_pipeline p, int32_t n, const fkl_tensor* ins
   for (int i = 0; i < n; ++i) {
     st = image_params(p->spec, &ins[i], rois, i, od, imgs[i]);
     if (st != FKL_OK) return st;
+  }
+  return FKL_OK;
+}
+
+}  // namespace
+
+namespace {
+
+// fkl_execute_batch with an optional device-side FP8 scale.
+fkl_status execute_batch_impl(fkl_pipeline p, int32_t n, const fkl_tensor* ins, const int32_t* rois,
+                              fkl_tensor* out, const float* scale_inv_dev, void* stream) {
+  OutDesc od;
+  std::vector<fkl::ResampleParams> imgs;
+  fkl_status st = validate_batch(p, n, ins, rois, out, od, imgs);
+  if (st != FKL_OK) return st;
+  od.p.scale_inv_dev = scale_inv_dev;
+  for (int start = 0; start < n; start += kBatchCap) {
+    LaunchCtx c;
+    c.spec = &p->spec;
+    c.shape = p->shape;
+    c.imgs = imgs.data() + start;
+    c.n = std::min(kBatchCap, n - start);
+    c.out = od.p;
+    c.out.base += start * od.p.img;
+    c.H = od.H;
+    c.W = od.W;
+    c.stream = static_cast<cudaStream_t>(stream);
+    c.all_exact2x = true;
+    for (int i = 0; i < c.n; ++i) c.all_exact2x = c.all_exact2x && (c.imgs[i].flags & fkl::kExact2x);
+    const cudaError_t e = launch_family(c);
+    if (e != cudaSuccess) return cuda_fail(e, "fused kernel launch");
   }
   return FKL_OK;
 }
@@ -511,38 +548,60 @@ const char* fkl_pipeline_kernel_name(fkl_pipeline p) { return p ? p->name.c_str(
 
 fkl_status fkl_execute_batch(fkl_pipeline p, int32_t n, const fkl_tensor* ins, const int32_t* rois,
                              fkl_tensor* out, void* stream) {
+  return execute_batch_impl(p, n, ins, rois, out, nullptr, stream);
+}
+
+
+fkl_status fkl_execute_batch_scaled(fkl_pipeline p, int32_t n, const fkl_tensor* ins, const int32_t* rois,
+                                    fkl_tensor* out, const float* scale_inv_dev, void* stream) {
+  if (!p) return fail(FKL_ERR_INVALID, "null pipeline");
+  if (p->spec.out_dtype != FKL_E4M3) return fail(FKL_ERR_INVALID, "scaled execution needs an E4M3 output");
+  if (!scale_inv_dev) return fail(FKL_ERR_INVALID, "scale pointer missing");
+  return execute_batch_impl(p, n, ins, rois, out, scale_inv_dev, stream);
+}
+
+fkl_status fkl_reduce_batch(fkl_pipeline p, int32_t n, const fkl_tensor* ins, const int32_t* rois,
+                            const fkl_tensor* out, float* stats, void* stream) {
+  if (!p) return fail(FKL_ERR_INVALID, "null pipeline");
+  if (p->spec.family != FAM_PACKED && p->spec.family != FAM_NV12)
+    return fail(FKL_ERR_UNSUPPORTED, "reductions run on float image chains");
+  if (!stats || reinterpret_cast<uintptr_t>(stats) % 16) return fail(FKL_ERR_INVALID, "stats must be 16-byte aligned");
   OutDesc od;
   std::vector<fkl::ResampleParams> imgs;
   fkl_status st = validate_batch(p, n, ins, rois, out, od, imgs);
   if (st != FKL_OK) return st;
-  for (int start = 0; start < n; start += kBatchCap) {
+  const cudaStream_t s = static_cast<cudaStream_t>(stream);
+  auto* acc = reinterpret_cast<fkl::ReduceAcc*>(reinterpret_cast<uint8_t*>(stats) + 64);
+  static_assert(sizeof(fkl::ReduceAcc) <= 64, "accumulator fits the stats buffer");
+  cudaError_t e = cudaMemsetAsync(acc, 0, sizeof(fkl::ReduceAcc), s);
+  if (e == cudaSuccess) e = cudaMemsetAsync(acc->min_key, 0xFF, sizeof(acc->min_key), s);
+  for (int start = 0; start < n && e == cudaSuccess; start += kBatchCap) {
     LaunchCtx c;
     c.spec = &p->spec;
     c.shape = p->shape;
     c.imgs = imgs.data() + start;
     c.n = std::min(kBatchCap, n - start);
     c.out = od.p;
-    c.out.base += start * od.p.img;
     c.H = od.H;
     c.W = od.W;
-    c.stream = static_cast<cudaStream_t>(stream);
+    c.stream = s;
     c.all_exact2x = true;
     for (int i = 0; i < c.n; ++i) c.all_exact2x = c.all_exact2x && (c.imgs[i].flags & fkl::kExact2x);
-    const cudaError_t e = launch_family(c);
-    if (e != cudaSuccess) return cuda_fail(e, "fused kernel launch");
+    e = launch_reduce(c, acc);
   }
-  return FKL_OK;
+  if (e == cudaSuccess) e = finalize_reduce(acc, static_cast<double>(n) * od.H * od.W, stats, s);
+  return e == cudaSuccess ? FKL_OK : cuda_fail(e, "reduction");
 }
 
 fkl_status fkl_execute(fkl_pipeline p, const fkl_tensor* in, fkl_tensor* out, void* stream) {
   if (!p) return fail(FKL_ERR_INVALID, "null pipeline");
   if (p->spec.family == FAM_VCHAIN) {
     int64_t n = 0;
-    const fkl_status st = check_linear(in, out, n);
+    const fkl_status st = check_linear(p->spec, in, out, n);
     if (st != FKL_OK) return st;
     if (n == 0) return FKL_OK;
-    const cudaError_t e = launch_vchain(p->spec, p->shape, static_cast<const float*>(in->data),
-                                        static_cast<float*>(out->data), n, static_cast<cudaStream_t>(stream));
+    const cudaError_t e = launch_vchain(p->spec, p->shape, in->data, static_cast<float*>(out->data), n,
+                                        static_cast<cudaStream_t>(stream));
     return e == cudaSuccess ? FKL_OK : cuda_fail(e, "vertical chain launch");
   }
   return fkl_execute_batch(p, 1, in, nullptr, out, stream);
@@ -574,11 +633,10 @@ fkl_status fkl_execute_batch_unfused(fkl_pipeline p, int32_t n, const fkl_tensor
   if (p->spec.family == FAM_VCHAIN) {
     if (n != 1) return fail(FKL_ERR_INVALID, "float32 tensor chains take one tensor (n = 1)");
     int64_t len = 0;
-    const fkl_status st = check_linear(ins, out, len);
+    const fkl_status st = check_linear(p->spec, ins, out, len);
     if (st != FKL_OK) return st;
     if (len == 0) return FKL_OK;
-    const cudaError_t e = launch_unfused_vchain(p->spec, static_cast<const float*>(ins->data),
-                                                static_cast<float*>(out->data), len, s);
+    const cudaError_t e = launch_unfused_vchain(p->spec, ins->data, static_cast<float*>(out->data), len, s);
     return e == cudaSuccess ? FKL_OK : cuda_fail(e, "unfused launch");
   }
   size_t need = 0;
@@ -700,11 +758,10 @@ fkl_status fkl_execute_batch_unfused_static(fkl_pipeline p, int32_t n, const fkl
   if (p->spec.family == FAM_VCHAIN) {  // one kernel per op, in place on `out`: no scratch
     if (n != 1) return fail(FKL_ERR_INVALID, "float32 tensor chains take one tensor (n = 1)");
     int64_t len = 0;
-    const fkl_status st = check_linear(ins, out, len);
+    const fkl_status st = check_linear(p->spec, ins, out, len);
     if (st != FKL_OK) return st;
     if (len == 0) return FKL_OK;
-    const cudaError_t e =
-        launch_unfused_vchain(p->spec, static_cast<const float*>(ins->data), static_cast<float*>(out->data), len, s);
+    const cudaError_t e = launch_unfused_vchain(p->spec, ins->data, static_cast<float*>(out->data), len, s);
     return e == cudaSuccess ? FKL_OK : cuda_fail(e, "unfused launch");
   }
   if (n < 0) return fail(FKL_ERR_INVALID, "negative batch size");

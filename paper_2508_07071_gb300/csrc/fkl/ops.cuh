@@ -573,11 +573,15 @@ struct OutParams {
   int64_t pitch;
   float scale_inv;  // FP8: the stored value is x * scale_inv
   int32_t aligned;  // 1: every run start is aligned for vector stores
+  const float* scale_inv_dev;  // FP8: if set, scale_inv is read from here (dynamic scaling)
 };
 
 template <class OutT>
 FKL_D float prescale(float x, const OutParams& p) {
-  if constexpr (std::is_same_v<OutT, e4m3_t>) return __fmul_rn(x, p.scale_inv);
+  if constexpr (std::is_same_v<OutT, e4m3_t>) {
+    const float inv = p.scale_inv_dev ? __ldg(p.scale_inv_dev) : p.scale_inv;
+    return __fmul_rn(x, inv);
+  }
   return x;
 }
 

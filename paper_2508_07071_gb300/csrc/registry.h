@@ -32,6 +32,7 @@ struct Spec {
   bool split = true;
   int32_t out_dtype = FKL_F32;
   float fp8_scale = 1.f;
+  bool vinput_u8 = false;       // vertical chain over a u8 tensor
   std::vector<int32_t> vkinds;  // vertical chain: 0 = Mul, 1 = Add
   std::vector<float> vconsts;
 };
@@ -62,9 +63,14 @@ cudaError_t launch_nv12_bf16(const LaunchCtx& c);
 cudaError_t launch_nv12_e4m3(const LaunchCtx& c);
 // Integer chains (k_int.cu).
 cudaError_t launch_int(const LaunchCtx& c);
+// ReduceDPP over the ROp and COps of a float image chain (k_reduce.cu):
+// accumulates into `acc` (initialised by the caller); `finalize_reduce`
+// turns the accumulator into the float statistics of include/fkl.h.
+cudaError_t launch_reduce(const LaunchCtx& c, fkl::ReduceAcc* acc);
+cudaError_t finalize_reduce(const fkl::ReduceAcc* acc, double count, float* stats, cudaStream_t st);
 // Vertical chain (k_vchain.cu): one fused launch per chunk of ops.
 constexpr int kVChainCap = 4096;
-cudaError_t launch_vchain(const Spec& s, const fkl_launch_shape& shape, const float* in, float* out,
+cudaError_t launch_vchain(const Spec& s, const fkl_launch_shape& shape, const void* in, float* out,
                           int64_t n, cudaStream_t stream);
 
 // Unfused reference form (k_unfused.cu): one kernel per op for one image;
@@ -72,7 +78,7 @@ cudaError_t launch_vchain(const Spec& s, const fkl_launch_shape& shape, const fl
 cudaError_t launch_unfused_image(const Spec& s, const fkl::ResampleParams& img,
                                  const fkl::OutParams& out, int z, int H, int W,
                                  void* ws0, void* ws1, cudaStream_t stream);
-cudaError_t launch_unfused_vchain(const Spec& s, const float* in, float* out, int64_t n,
+cudaError_t launch_unfused_vchain(const Spec& s, const void* in, float* out, int64_t n,
                                   cudaStream_t stream);
 
 // Launch shapes compiled for a family/dtype (the autotuner's search space).

@@ -143,6 +143,7 @@ __global__ void __launch_bounds__(kThreads) serve_kernel(const __grid_constant__
     wp.pitch = a.pitch;
     wp.scale_inv = a.scale_inv;
     wp.aligned = a.aligned;
+    wp.scale_inv_dev = nullptr;
     for (int it = threadIdx.x; it < items; it += blockDim.x) {
       const int y = it / cols;
       const int x0 = (it - y * cols) * kV;

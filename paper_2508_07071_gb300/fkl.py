@@ -27,6 +27,7 @@ FKL_LAYOUT_LINEAR, FKL_LAYOUT_HWC, FKL_LAYOUT_NV12, FKL_LAYOUT_NCHW, FKL_LAYOUT_
 FKL_OP_READ_U8C3 = 1
 FKL_OP_READ_NV12 = 2
 FKL_OP_READ_F32 = 3
+FKL_OP_READ_U8 = 4
 FKL_OP_CROP = 10
 FKL_OP_RESIZE = 11
 FKL_OP_LETTERBOX = 12
@@ -146,6 +147,12 @@ EXPORTS = {
     "fkl_server_release": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_uint64]),
     "fkl_server_get_stats": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(fkl_server_stats)]),
     "fkl_server_destroy": (None, [ctypes.c_void_p]),
+    "fkl_reduce_batch": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int32, ctypes.POINTER(fkl_tensor),
+                                        ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(fkl_tensor),
+                                        ctypes.c_void_p, ctypes.c_void_p]),
+    "fkl_execute_batch_scaled": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int32, ctypes.POINTER(fkl_tensor),
+                                                ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(fkl_tensor),
+                                                ctypes.c_void_p, ctypes.c_void_p]),
     "fkl_version": (ctypes.c_char_p, []),
 }
 
@@ -198,6 +205,10 @@ def read_nv12():
 
 def read_f32():
     return _desc(FKL_OP_READ_F32)
+
+
+def read_u8():
+    return _desc(FKL_OP_READ_U8)
 
 
 def crop(x, y, w, h):
@@ -395,6 +406,27 @@ def fkl_execute_batch(p: int, ins: Sequence[fkl_tensor], rois, out: fkl_tensor, 
     keep = _rois(rois)
     _check(_lib.fkl_execute_batch(p, len(ins), arr, keep[1] if keep else None, ctypes.byref(out),
                                   _stream(stream)))
+
+
+FKL_REDUCE_STATS_BYTES = 128
+
+
+def fkl_reduce_batch(p: int, ins: Sequence[fkl_tensor], rois, out: fkl_tensor, stats_ptr: int,
+                     stream=None) -> None:
+    """ReduceDPP: stats (device, 128 bytes) = min[3], max[3], mean[3], amax,
+    s = amax/448, 1/s."""
+    arr = (fkl_tensor * max(1, len(ins)))(*ins)
+    keep = _rois(rois)
+    _check(_lib.fkl_reduce_batch(p, len(ins), arr, keep[1] if keep else None, ctypes.byref(out), stats_ptr,
+                                 _stream(stream)))
+
+
+def fkl_execute_batch_scaled(p: int, ins: Sequence[fkl_tensor], rois, out: fkl_tensor, scale_inv_ptr: int,
+                             stream=None) -> None:
+    arr = (fkl_tensor * max(1, len(ins)))(*ins)
+    keep = _rois(rois)
+    _check(_lib.fkl_execute_batch_scaled(p, len(ins), arr, keep[1] if keep else None, ctypes.byref(out),
+                                         scale_inv_ptr, _stream(stream)))
 
 
 def fkl_unfused_workspace_bytes(p: int, ins: Sequence[fkl_tensor], rois, out: fkl_tensor) -> int:

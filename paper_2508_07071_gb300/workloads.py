@@ -46,9 +46,9 @@ def nv12_letterbox_chain(out_dtype, out=640, pad=114.0, scale=None):
             F.write_split(out_dtype, scale)]
 
 
-def vertical_chain(kinds, consts):
-    """READ_F32 -> (MUL|ADD)* -> WRITE_PACKED(F32)."""
-    ops = [F.read_f32()]
+def vertical_chain(kinds, consts, u8_input=False):
+    """READ_F32 (or READ_U8) -> (MUL|ADD)* -> WRITE_PACKED(F32)."""
+    ops = [F.read_u8() if u8_input else F.read_f32()]
     for k, c in zip(kinds, consts):
         ops.append(F.scalar_op(F.FKL_OP_ADD if k == 1 else F.FKL_OP_MUL, float(c)))
     ops.append(F.write_packed(F.FKL_F32))

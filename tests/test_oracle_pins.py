@@ -424,3 +424,16 @@ def test_lowp_rule_accepts_roundings_inside_the_f32_bound_only():
     # a value 1e-5 away near zero fails
     with pytest.raises(AssertionError):
         check_lowp(O.round_f16(o - np.array([1e-5, 0, 0])), o, "f16")
+
+
+def test_reduce_stats_closed_forms():
+    v = np.zeros((2, 3, 4, 5))
+    v[:, 0] = 7.0
+    v[:, 1, 0, 0] = -3.0          # one negative pixel per image in channel 1
+    v[:, 2] = np.arange(20).reshape(4, 5)
+    st = O.reduce_stats(v)
+    assert st["min"].tolist() == [7.0, -3.0, 0.0]
+    assert st["max"].tolist() == [7.0, 0.0, 19.0]
+    np.testing.assert_allclose(st["mean"], [7.0, -3.0 / 20, 9.5])
+    assert st["amax"] == 19.0 and st["scale"] == 19.0 / 448
+    assert O.reduce_stats(np.zeros((3, 2, 2)))["scale"] == 1.0

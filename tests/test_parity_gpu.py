@@ -441,3 +441,71 @@ def test_host_executor_matches_device_path(F, W):
                                      F.as_fkl(out2, F.FKL_LAYOUT_NCHW))
     finally:
         F.fkl_host_executor_destroy(e)
+
+
+@pytest.mark.parametrize("L", [0, 3, 200, 4101])
+def test_vertical_chain_u8_input_bit_exact(F, W, L):
+    n = 50 * 60 * 120 + 5                               # ragged tail
+    x = synth.packed_image(15, 1, n, 1).reshape(-1)
+    kinds, consts = synth.chain_constants(5, L)
+    p = F.Pipeline(W.vertical_chain(kinds, consts, u8_input=True))
+    assert "ReadU8" in p.kernel_name
+    xin = torch.from_numpy(x).cuda()
+    want = O.vertical_chain_f32(x.astype(np.float32), kinds, consts).view(np.uint32)
+    for shape in F.fkl_pipeline_shapes(p.handle)[:: 3 if L > 1000 else 1]:
+        F.fkl_pipeline_set_shape(p.handle, shape)
+        out = torch.full((n,), float("nan"), device="cuda")
+        F.fkl_execute(p.handle, F.as_fkl(xin), F.as_fkl(out))
+        torch.cuda.synchronize()
+        assert np.array_equal(out.cpu().numpy().view(np.uint32), want), shape
+    if L <= 200:
+        out2 = torch.full((n,), float("nan"), device="cuda")
+        F.fkl_execute_batch_unfused(p.handle, [F.as_fkl(xin)], None, F.as_fkl(out2), 0, 0)
+        torch.cuda.synchronize()
+        assert np.array_equal(out2.cpu().numpy().view(np.uint32), want)
+    with pytest.raises(F.FklError):                     # a u8 chain refuses float input
+        F.fkl_execute(p.handle, F.as_fkl(torch.zeros(n, device="cuda")), F.as_fkl(out))
+
+
+def test_reduce_stats_and_dynamic_fp8(F, W):
+    frames = synth.nv12_frames(17, 3, 720, 1280)
+    dev = torch.from_numpy(frames).cuda()
+    ins = [F.as_fkl(dev[i], F.FKL_LAYOUT_NV12) for i in range(3)]
+    p = F.Pipeline(W.nv12_letterbox_chain(F.FKL_E4M3, scale=1.0))
+    out = torch.zeros((3, 3, 640, 640), dtype=torch.float8_e4m3fn, device="cuda")
+    o = F.as_fkl(out, F.FKL_LAYOUT_NCHW)
+    stats = torch.zeros(32, device="cuda")
+    F.fkl_reduce_batch(p.handle, ins, None, o, stats.data_ptr())
+    F.fkl_execute_batch_scaled(p.handle, ins, None, o, stats.data_ptr() + 11 * 4)
+    torch.cuda.synchronize()
+    st = stats.cpu().numpy().astype(np.float64)
+    vals = np.stack([O.preprocess_nv12(f, 640, 640, pad=114.0, mul=1 / 255) for f in frames])
+    want = O.reduce_stats(vals)
+    check_f32(st[0:3], want["min"], "min")
+    check_f32(st[3:6], want["max"], "max")
+    np.testing.assert_allclose(st[6:9], want["mean"], rtol=1e-6)
+    check_f32(st[9], want["amax"], "amax")
+    check_f32(st[10], want["scale"], "scale")
+    # the stored codes are the oracle values quantised with the kernel's scale
+    check_lowp(to_numpy(out), vals / np.float32(st[10]), "e4m3", 1.0, "dynamic fp8")
+    assert out.view(torch.uint8).max().item() == 0x7E  # amax maps onto 448
+
+
+def test_reduce_stats_normalised_packed(F, W):
+    src = synth.packed_image(18, 300, 500)
+    rois = np.array([[0, 0, 500, 300], [10, 20, 200, 150]], np.int32)
+    d = torch.from_numpy(src).cuda()
+    p = F.Pipeline(W.normalize_chain(224, 224))
+    out = torch.zeros((2, 3, 224, 224), device="cuda")
+    stats = torch.zeros(32, device="cuda")
+    F.fkl_reduce_batch(p.handle, [F.as_fkl(d)] * 2, rois, F.as_fkl(out, F.FKL_LAYOUT_NCHW), stats.data_ptr())
+    torch.cuda.synchronize()
+    st = stats.cpu().numpy().astype(np.float64)
+    vals = O.preprocess_packed_batch([src] * 2, rois, 224, 224, swap=True, mul=1 / 255,
+                                     sub=W.IMAGENET_MEAN, div=W.IMAGENET_STD)
+    want = O.reduce_stats(vals)
+    check_f32(st[0:3], want["min"], "min")
+    check_f32(st[3:6], want["max"], "max")
+    np.testing.assert_allclose(st[6:9], want["mean"], rtol=1e-5, atol=1e-6)
+    check_f32(st[9], want["amax"], "amax")
+    assert float(out.abs().sum()) == 0.0               # the reduction writes no output
