@@ -261,6 +261,21 @@ def make_workload(args, F, W, synth, metrics, torch):
 # ------------------------------------------------------------------ timing
 
 
+def aggregate_ranks(dev_ms: float, bytes_per_rank: int, world: int):
+    """Whole-job timing across ranks: the slowest rank's device time and the
+    bytes all ranks processed (weak scaling: each rank runs its own batch)."""
+    if world <= 1:
+        return dev_ms, bytes_per_rank
+    import torch
+    import torch.distributed as dist
+    dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([dev_ms], dtype=torch.float64, device=dev)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    b = torch.tensor([bytes_per_rank], dtype=torch.float64, device=dev)
+    dist.all_reduce(b, op=dist.ReduceOp.SUM)
+    return float(t.item()), int(b.item())
+
+
 def time_steps(torch, fn, K, stream, between=None):
     """Device time of K calls, each bracketed by events on `stream`; an
     optional `between` (L2 flush) runs outside the bracketed regions."""
@@ -317,11 +332,7 @@ def run_ours(args):
         sampler.stop()
         if world > 1:
             dist.barrier()
-        dev_ms = float(np.sum(times))
-        if world > 1:
-            t = torch.tensor([dev_ms], device="cuda")
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            dev_ms = float(t.item())
+        dev_ms, total_bytes = aggregate_ranks(float(np.sum(times)), wl.bytes, world)
         ms_per_step = dev_ms / args.steps
         kernel_ms = float(np.mean(times)) / wl.launches_per_step
 
@@ -356,7 +367,6 @@ def run_ours(args):
                 link_ms = float(np.mean(time_steps(torch, wl.link_copy, ke, stream)))
 
     peak, peak_kind = measured_peaks()
-    total_bytes = wl.bytes * world
     value = total_bytes / (ms_per_step * 1e-3) / 1e9
     achieved = wl.bytes / wl.launches_per_step / (kernel_ms * 1e-3) / 1e9
     line = {

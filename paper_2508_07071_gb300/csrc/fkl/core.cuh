@@ -110,6 +110,36 @@ FKL_D auto apply_chain(const T& v, const Tuple<H, Ts...>& t) {
   return apply_chain(apply_one(t.head, v), t.tail);
 }
 
+// Pair form of a chain (see F3x2 in ops.cuh): available when every COp has
+// an exec_pair; the DPP then runs the chain on two pixels per instruction.
+template <class I, class = void>
+struct HasPair : std::false_type {};
+template <class I>
+struct HasPair<I, std::void_t<decltype(&I::Operation::exec_pair)>> : std::true_type {};
+
+template <class Tup>
+struct ChainHasPair;
+template <>
+struct ChainHasPair<Tuple<>> : std::true_type {};
+template <class H, class... Ts>
+struct ChainHasPair<Tuple<H, Ts...>> {
+  static constexpr bool value = HasPair<H>::value && ChainHasPair<Tuple<Ts...>>::value;
+};
+
+template <class P>
+FKL_D P apply_chain_pair(const P& v, const Tuple<>&) {
+  return v;
+}
+template <class P, class H, class... Ts>
+FKL_D P apply_chain_pair(const P& v, const Tuple<H, Ts...>& t) {
+  using Op = typename H::Operation;
+  if constexpr (std::is_same_v<typename Op::InstanceType, UnaryType>) {
+    return apply_chain_pair(Op::exec_pair(v), t.tail);
+  } else {
+    return apply_chain_pair(Op::exec_pair(v, t.head.params), t.tail);
+  }
+}
+
 // Result type of a chain of COps applied to T.
 template <class T, class Tup>
 struct ChainResult;

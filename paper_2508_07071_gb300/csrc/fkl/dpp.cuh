@@ -55,8 +55,14 @@ __global__ void __launch_bounds__(256) transform2d_kernel(const __grid_constant_
     const int y = ybase + r;
     if (y < a.H) {
       WT out[V];
+      if constexpr (ChainHasPair<Cops>::value && std::is_same_v<RT, F3> && std::is_same_v<WT, F3> && V % 2 == 0) {
 #pragma unroll
-      for (int k = 0; k < V; ++k) out[k] = apply_chain(in[r][k], a.cops);
+        for (int k = 0; k < V; k += 2)
+          unpack_pair(apply_chain_pair(pack_pair(in[r][k], in[r][k + 1]), a.cops), out[k], out[k + 1]);
+      } else {
+#pragma unroll
+        for (int k = 0; k < V; ++k) out[k] = apply_chain(in[r][k], a.cops);
+      }
       W::template exec_span<V>(Point{x0, y, z}, n, out, a.wp);
     }
   }
@@ -67,8 +73,7 @@ struct Shape2D {
 };
 
 template <int V, int RY, class RB, class W, class Cops>
-cudaError_t launch_transform2d(const Args2D<RB, W, Cops>& a, int batch, int tx, int ty,
-                               cudaStream_t s) {
+cudaError_t launch_transform2d(Args2D<RB, W, Cops>& a, int batch, int tx, int ty, cudaStream_t s) {
   const int cols = (a.W_ + V - 1) / V;
   const int rows = (a.H + RY - 1) / RY;
   const dim3 block(tx, ty, 1);

@@ -489,6 +489,21 @@ struct BatchRead {
 // Compute Operations
 // ===========================================================================
 
+// Two pixels' channels, one pixel per lane of a packed pair (f32x2): the
+// form in which a DPP may run elementwise COps on Blackwell's packed FP32
+// instructions. An Op that offers `exec_pair` computes exactly `exec` on
+// each lane.
+struct F3x2 {
+  F2 v[3];
+};
+FKL_D F3x2 pack_pair(const F3& a, const F3& b) {
+  return F3x2{{f2(a.v[0], b.v[0]), f2(a.v[1], b.v[1]), f2(a.v[2], b.v[2])}};
+}
+FKL_D void unpack_pair(const F3x2& p, F3& a, F3& b) {
+#pragma unroll
+  for (int c = 0; c < 3; ++c) f2split(p.v[c], a.v[c], b.v[c]);
+}
+
 // ColorConvert BGR <-> RGB: a register permutation.
 template <class P>
 struct SwapRB {
@@ -501,6 +516,7 @@ struct SwapRB {
     o.v[2] = x.v[0];
     return o;
   }
+  static FKL_D F3x2 exec_pair(const F3x2& x) { return F3x2{{x.v[2], x.v[1], x.v[0]}}; }
 };
 
 struct C3Params {
@@ -515,6 +531,9 @@ struct Mul3 {
   static FKL_D F3 exec(const F3& x, const ParamsType& p) {
     return F3{{__fmul_rn(x.v[0], p.c[0]), __fmul_rn(x.v[1], p.c[1]), __fmul_rn(x.v[2], p.c[2])}};
   }
+  static FKL_D F3x2 exec_pair(const F3x2& x, const ParamsType& p) {
+    return F3x2{{f2mul(x.v[0], f2s(p.c[0])), f2mul(x.v[1], f2s(p.c[1])), f2mul(x.v[2], f2s(p.c[2]))}};
+  }
 };
 struct Sub3 {
   using InstanceType = BinaryType;
@@ -523,6 +542,9 @@ struct Sub3 {
   using ParamsType = C3Params;
   static FKL_D F3 exec(const F3& x, const ParamsType& p) {
     return F3{{__fsub_rn(x.v[0], p.c[0]), __fsub_rn(x.v[1], p.c[1]), __fsub_rn(x.v[2], p.c[2])}};
+  }
+  static FKL_D F3x2 exec_pair(const F3x2& x, const ParamsType& p) {
+    return F3x2{{f2sub(x.v[0], f2s(p.c[0])), f2sub(x.v[1], f2s(p.c[1])), f2sub(x.v[2], f2s(p.c[2]))}};
   }
 };
 // IEEE division. `on` = 0 passes the value through untouched (a chain
@@ -604,6 +626,19 @@ struct WriteSplit {
   static FKL_D void exec_span(const Point& pt, int n, const InputType (&v)[V], const ParamsType& p) {
     uint8_t* q = p.base + pt.z * p.img + pt.y * p.pitch + static_cast<int64_t>(pt.x) * B;
     if (n == V && p.aligned) {
+      if constexpr (std::is_same_v<OutT, e4m3_t> && V % 2 == 0) {
+        // FP8 scaling two values per packed multiply (same bits as prescale)
+        const float inv = p.scale_inv_dev ? __ldg(p.scale_inv_dev) : p.scale_inv;
+        const F2 inv2 = f2s(inv);
+#pragma unroll
+        for (int c = 0; c < C; ++c) {
+          float run[V];
+#pragma unroll
+          for (int k = 0; k < V; k += 2) f2split(f2mul(f2(v[k].v[c], v[k + 1].v[c]), inv2), run[k], run[k + 1]);
+          store_run<OutT, V>(q + c * p.plane, run);
+        }
+        return;
+      }
 #pragma unroll
       for (int c = 0; c < C; ++c) {
         float run[V];

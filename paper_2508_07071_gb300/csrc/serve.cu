@@ -283,12 +283,12 @@ struct fkl_server_s {
   HostCtl* hc_dev = nullptr;
   DevCtl* dc = nullptr;
   int* rem_staging = nullptr;  // pinned, one int per slot
-  uint8_t* ws = nullptr;       // unfused-mode workspace
+  uint8_t* ws[2] = {nullptr, nullptr};  // unfused-mode workspace per copy stream
   size_t ws_bytes = 0;
   KernelFn kernel = nullptr;
   KArgs kargs{};
   int grid = 0;
-  cudaStream_t s_copy = nullptr;
+  cudaStream_t s_copy[2] = {nullptr, nullptr};  // requests alternate between two copy engines
   std::vector<cudaStream_t> s_kernel;
   std::thread thread;
   std::mutex mu;
@@ -355,6 +355,7 @@ bool admit(fkl_server_s* s, Request& r) {
   r.in_bytes = in_bytes;
   r.seq = s->next_seq++;
   uint8_t* base = s->arena_base + off;
+  const cudaStream_t cs = s->s_copy[r.seq & 1];
   r.rp.resize(r.n);
   cudaError_t ce = cudaSuccess;
   std::vector<fkl_tensor> dev_in(r.n);
@@ -364,9 +365,8 @@ bool admit(fkl_server_s* s, Request& r) {
     const int64_t hp = h.pitch_bytes ? h.pitch_bytes : row;
     const int64_t dp = row;
     ce = hp == row ? cudaMemcpyAsync(base + offs[i], h.data, static_cast<size_t>(row * h.dims[0]),
-                                     cudaMemcpyHostToDevice, s->s_copy)
-                   : cudaMemcpy2DAsync(base + offs[i], dp, h.data, hp, row, h.dims[0], cudaMemcpyHostToDevice,
-                                       s->s_copy);
+                                     cudaMemcpyHostToDevice, cs)
+                   : cudaMemcpy2DAsync(base + offs[i], dp, h.data, hp, row, h.dims[0], cudaMemcpyHostToDevice, cs);
     fkl::ResampleParams& p = r.rp[i];
     std::memset(&p, 0, sizeof(p));
     p.src = base + offs[i];
@@ -384,9 +384,9 @@ bool admit(fkl_server_s* s, Request& r) {
   if (ce == cudaSuccess && s->cfg.mode == FKL_SERVE_PERSISTENT) {
     s->rem_staging[r.slot] = r.n;
     ce = cudaMemcpyAsync(&s->dc->remaining[r.slot], &s->rem_staging[r.slot], sizeof(int), cudaMemcpyHostToDevice,
-                         s->s_copy);
+                         cs);
   }
-  if (ce == cudaSuccess) ce = cudaEventRecord(r.ev_copy, s->s_copy);
+  if (ce == cudaSuccess) ce = cudaEventRecord(r.ev_copy, cs);
   if (ce == cudaSuccess && s->cfg.mode != FKL_SERVE_PERSISTENT) {
     fkl_tensor out{};
     out.data = base + in_bytes;
@@ -399,11 +399,11 @@ bool admit(fkl_server_s* s, Request& r) {
     out.layout = FKL_LAYOUT_NCHW;
     const fkl_status st =
         s->cfg.mode == FKL_SERVE_BATCH
-            ? fkl_execute_batch(s->p, r.n, dev_in.data(), nullptr, &out, s->s_copy)
-            : fkl_execute_batch_unfused(s->p, r.n, dev_in.data(), nullptr, &out, s->ws, s->ws_bytes, s->s_copy);
+            ? fkl_execute_batch(s->p, r.n, dev_in.data(), nullptr, &out, cs)
+            : fkl_execute_batch_unfused(s->p, r.n, dev_in.data(), nullptr, &out, s->ws[r.seq & 1], s->ws_bytes, cs);
     if (st != FKL_OK) s->thread_error = fkl_last_error();
     s->stats.kernel_launches += s->cfg.mode == FKL_SERVE_BATCH ? 1 : 0;
-    ce = cudaEventRecord(r.ev_done, s->s_copy);
+    ce = cudaEventRecord(r.ev_done, cs);
   }
   if (ce != cudaSuccess) s->thread_error = cudaGetErrorString(ce);
   r.state = 1;
@@ -501,17 +501,20 @@ void teardown(fkl_server_s* s) {
   }
   for (cudaStream_t st : s->s_kernel)
     if (st) cudaStreamSynchronize(st);
-  if (s->s_copy) cudaStreamSynchronize(s->s_copy);
+  for (cudaStream_t st : s->s_copy)
+    if (st) cudaStreamSynchronize(st);
   for (auto& kv : s->reqs) {
     if (kv.second.ev_copy) cudaEventDestroy(kv.second.ev_copy);
     if (kv.second.ev_done) cudaEventDestroy(kv.second.ev_done);
   }
   for (cudaStream_t st : s->s_kernel)
     if (st) cudaStreamDestroy(st);
-  if (s->s_copy) cudaStreamDestroy(s->s_copy);
+  for (cudaStream_t st : s->s_copy)
+    if (st) cudaStreamDestroy(st);
   if (s->arena_base) cudaFree(s->arena_base);
   if (s->dc) cudaFree(s->dc);
-  if (s->ws) cudaFree(s->ws);
+  for (uint8_t* w : s->ws)
+    if (w) cudaFree(w);
   if (s->hc) cudaFreeHost(s->hc);
   if (s->rem_staging) cudaFreeHost(s->rem_staging);
   delete s->arena;
@@ -556,9 +559,9 @@ fkl_status fkl_server_create(fkl_pipeline p, const fkl_server_config* cfg, fkl_s
   if (ce == cudaSuccess) ce = cudaHostAlloc(reinterpret_cast<void**>(&s->rem_staging), kMaxSlots * sizeof(int), 0);
   if (ce == cudaSuccess && cfg->mode == FKL_SERVE_UNFUSED) {
     s->ws_bytes = 2 * up(static_cast<size_t>(s->H) * s->W * 12, 256);
-    ce = cudaMalloc(reinterpret_cast<void**>(&s->ws), s->ws_bytes);
+    for (int i = 0; i < 2 && ce == cudaSuccess; ++i) ce = cudaMalloc(reinterpret_cast<void**>(&s->ws[i]), s->ws_bytes);
   }
-  if (ce == cudaSuccess) ce = cudaStreamCreateWithFlags(&s->s_copy, cudaStreamNonBlocking);
+  for (int i = 0; i < 2 && ce == cudaSuccess; ++i) ce = cudaStreamCreateWithFlags(&s->s_copy[i], cudaStreamNonBlocking);
   for (int i = 0; i < 4 && ce == cudaSuccess; ++i) {
     cudaStream_t st = nullptr;
     ce = cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking);
