@@ -509,3 +509,23 @@ def test_reduce_stats_normalised_packed(F, W):
     np.testing.assert_allclose(st[6:9], want["mean"], rtol=1e-5, atol=1e-6)
     check_f32(st[9], want["amax"], "amax")
     assert float(out.abs().sum()) == 0.0               # the reduction writes no output
+
+
+@pytest.mark.parametrize("fmt", ["e4m3", "f16"])
+def test_nv12_full_batch_autotuned_sampled(F, W, fmt):
+    """The bench's configuration: 256 frames, autotuned launch shape."""
+    cfg = W.NV12
+    frames = synth.nv12_frames(3, cfg["n"], cfg["h"], cfg["w"])
+    dev = torch.from_numpy(frames).cuda()
+    p = F.Pipeline(W.nv12_letterbox_chain(code(F, fmt)))
+    out = torch.zeros((cfg["n"], 3, 640, 640), dtype=tdtype(fmt), device="cuda")
+    ins = [F.as_fkl(dev[i], F.FKL_LAYOUT_NV12) for i in range(cfg["n"])]
+    o = F.as_fkl(out, F.FKL_LAYOUT_NCHW)
+    best, _ = F.fkl_pipeline_autotune(p.handle, ins, None, o, reps=3)
+    out.zero_()
+    F.fkl_execute_batch(p.handle, ins, None, o)
+    torch.cuda.synchronize()
+    scale = W.E4M3_SCALE if fmt == "e4m3" else 1.0
+    for i in [0, 100, cfg["n"] - 1]:
+        want = O.preprocess_nv12(frames[i], 640, 640, pad=114.0, mul=1 / 255)
+        check_output(out[i], want, fmt, scale, f"{fmt} frame {i} shape {best}")
