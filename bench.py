@@ -30,17 +30,10 @@ METRIC = "Fused GB/s vs 8 TB/s HBM & speedup over unfused per-op kernels, same G
 
 
 def kernel_source_hash() -> str:
-    """Hash of every CUDA source and header of the library: a stored ncu
-    traffic figure applies only to the kernel build it was measured on."""
-    import hashlib
-    h = hashlib.sha256()
-    base = os.path.join(ROOT, "paper_2508_07071_gb300", "csrc")
-    for d, _, files in sorted(os.walk(base)):
-        for f in sorted(files):
-            if f.endswith((".cu", ".cuh", ".h")):
-                h.update(f.encode())
-                h.update(open(os.path.join(d, f), "rb").read())
-    return h.hexdigest()[:16]
+    """Hash of the kernel sources and build flags: a stored ncu traffic
+    figure applies only to the kernel build it was measured on."""
+    from paper_2508_07071_gb300.ncu_traffic import source_hash
+    return source_hash()
 
 
 def measured_traffic(key: str):

@@ -405,7 +405,18 @@ FKL_API const char* fkl_pipeline_kernel_name(fkl_pipeline p);
  * Float32 tensor chains: `vec` elements per thread and iteration (8, 16 or
  * 32), TX threads per block (TY = 1); RY = 1 runs a persistent grid of
  * (2048 / TX) blocks per SM striding over the tensor, RY = 0 one block per
- * TX * vec elements. */
+ * TX * vec elements.
+ * NV12 chains with a split output, RY <= 0: the row-staged kernel (paper
+ * §IV-C DPP on the bulk-copy engine). Jobs of TY output rows; a persistent
+ * grid of TX-thread CTAs copies each job's source rows (two luma rows and one
+ * chroma row per output row) into a shared-memory ring of -RY stages (RY = 0:
+ * as many as fill about 64 KB) with asynchronous bulk copies and computes
+ * from there. It runs when every image of a launch is an
+ * exact 2x downscale of a 16-byte aligned window (x offset a multiple of 16,
+ * even y offset, pitch a multiple of 16, 16-byte aligned base) that fills the
+ * output width, and the output width is a multiple of `vec`; any other launch
+ * of the pipeline runs the register kernel with a 32 x 8 block and RY = 1.
+ * Both give the same bytes. */
 typedef struct {
   int32_t vec;      /* pixels (elements) per thread along x               */
   int32_t tx, ty;   /* threads per block along x and y                    */
@@ -444,6 +455,14 @@ FKL_API fkl_status fkl_pipeline_autotune_ex(fkl_pipeline p, int32_t n, const fkl
                                             const int32_t* rois, fkl_tensor* out, void* stream,
                                             int32_t reps, void (*before)(void* user), void* user,
                                             fkl_launch_shape* best, float* best_us);
+
+/* Reads and clears the flag the fused kernels' bounded device waits set when
+ * one gives up (the row-staged NV12 kernel waits on its own copies; a wait
+ * longer than 1 s stops that CTA, whose outputs are then incomplete).
+ * Synchronises the current device first. Returns FKL_ERR_TIMEOUT if the flag
+ * was set since the last call on this device, FKL_OK if not, FKL_ERR_CUDA if a
+ * CUDA call failed (the message has it). */
+FKL_API fkl_status fkl_device_check(void);
 
 /* Library version string. */
 FKL_API const char* fkl_version(void);

@@ -20,8 +20,13 @@ BUILD = os.path.join(PKG, "_build")
 LIB = os.path.join(PKG, "libfkl.so")
 
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
-NVCC_FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "-Xcompiler", "-fvisibility=hidden",
-              "-Xptxas", "-warn-spills", "--diag-suppress=177"]
+# -fmad=false: plain float expressions are not contracted into multiply-adds;
+# the kernels spell out each one they want (fmaf / fma.rn) and round every
+# other operation where written (_rn intrinsics). The flag does not stop the
+# assembler from fusing a packed f32x2 multiply into a packed add that
+# consumes it, so the kernels never write that pair (see ops.cuh).
+NVCC_FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-fmad=false", "-Xcompiler", "-fPIC", "-Xcompiler",
+              "-fvisibility=hidden", "-Xptxas", "-warn-spills", "--diag-suppress=177"]
 
 
 def nvcc() -> str:

@@ -327,6 +327,10 @@ int sm_count() {
 
 namespace {
 const int kBlocks[][2] = {{8, 16}, {16, 8}, {16, 16}, {32, 4}, {32, 8}, {64, 2}, {64, 4}, {128, 1}, {128, 2}};
+// Row-staged NV12 shapes {threads, rows per job, stages}: the fastest of a
+// 24-point sweep (threads 128/256, rows 2/4/8, stages 2/3/4/6) on 256 frames
+// 1280x720 -> 640x640; deeper rings and longer jobs only lowered occupancy.
+const int kStaged[][3] = {{128, 4, 2}, {128, 2, 2}, {128, 4, 3}, {256, 8, 2}};
 }
 // ---------------------------------------------------------------------------
 // Scratch for fkl_execute_batch_unfused_static: a fixed device array that
@@ -337,8 +341,12 @@ const int kBlocks[][2] = {{8, 16}, {16, 8}, {16, 16}, {32, 4}, {32, 8}, {64, 2},
 constexpr size_t kStaticScratchBytes = size_t(32) << 20;  // 32 MiB
 static __device__ __align__(256) uint8_t g_unfused_scratch[kStaticScratchBytes];
 
+// Set to 1 by a bounded device wait that gave up (fkl_device_check).
+static __device__ int g_device_error;
+
 namespace {
 std::mutex g_scratch_mu;
+void* g_error_ptr[64] = {nullptr};
 void* g_scratch_ptr[64] = {nullptr};
 
 // Device address of g_unfused_scratch on the current device, looked up once
@@ -359,6 +367,22 @@ cudaError_t static_scratch(void** out) {
   return cudaSuccess;
 }
 }  // namespace
+
+cudaError_t device_error_flag(int** out) {
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  if (dev < 0 || dev >= 64) return cudaErrorInvalidDevice;
+  std::lock_guard<std::mutex> lk(g_scratch_mu);
+  if (!g_error_ptr[dev]) {
+    void* ptr = nullptr;
+    e = cudaGetSymbolAddress(&ptr, g_device_error);
+    if (e != cudaSuccess) return e;
+    g_error_ptr[dev] = ptr;
+  }
+  *out = static_cast<int*>(g_error_ptr[dev]);
+  return cudaSuccess;
+}
 
 
 std::vector<fkl_launch_shape> shapes_for(const Spec& s) {
@@ -382,6 +406,11 @@ std::vector<fkl_launch_shape> shapes_for(const Spec& s) {
     for (int ry : {1, 2}) {
       if (v > 8 && ry > 1) continue;  // not compiled (register budget)
       for (const auto& b : kBlocks) out.push_back(fkl_launch_shape{v, b[0], b[1], ry});
+    }
+  if (s.family == FAM_NV12 && s.split)  // row-staged kernel: {vec, threads, rows per job, -stages}
+    for (int v : vecs) {
+      if (v % 8) continue;
+      for (const auto& st : kStaged) out.push_back(fkl_launch_shape{v, st[0], st[1], -st[2]});
     }
   return out;
 }
@@ -495,6 +524,11 @@ fkl_status execute_batch_impl(fkl_pipeline p, int32_t n, const fkl_tensor* ins, 
   fkl_status st = validate_batch(p, n, ins, rois, out, od, imgs);
   if (st != FKL_OK) return st;
   od.p.scale_inv_dev = scale_inv_dev;
+  int* err_flag = nullptr;
+  if (n > 0 && p->shape.ry <= 0 && p->spec.family == FAM_NV12) {
+    const cudaError_t e = device_error_flag(&err_flag);
+    if (e != cudaSuccess) return cuda_fail(e, "device flag lookup");
+  }
   for (int start = 0; start < n; start += kBatchCap) {
     LaunchCtx c;
     c.spec = &p->spec;
@@ -508,6 +542,7 @@ fkl_status execute_batch_impl(fkl_pipeline p, int32_t n, const fkl_tensor* ins, 
     c.stream = static_cast<cudaStream_t>(stream);
     c.all_exact2x = true;
     for (int i = 0; i < c.n; ++i) c.all_exact2x = c.all_exact2x && (c.imgs[i].flags & fkl::kExact2x);
+    c.device_error = err_flag;
     const cudaError_t e = launch_family(c);
     if (e != cudaSuccess) return cuda_fail(e, "fused kernel launch");
   }
@@ -541,6 +576,18 @@ fkl_status fkl_pipeline_create(const fkl_op_desc* ops, int32_t n_ops, fkl_pipeli
 void fkl_pipeline_destroy(fkl_pipeline p) { delete p; }
 
 const char* fkl_last_error(void) { return t_error.c_str(); }
+
+fkl_status fkl_device_check(void) {
+  int* flag = nullptr;
+  cudaError_t e = device_error_flag(&flag);
+  if (e == cudaSuccess) e = cudaDeviceSynchronize();
+  int v = 0;
+  if (e == cudaSuccess) e = cudaMemcpy(&v, flag, sizeof(int), cudaMemcpyDeviceToHost);
+  if (e == cudaSuccess && v) e = cudaMemset(flag, 0, sizeof(int));
+  if (e != cudaSuccess) return cuda_fail(e, "device check");
+  if (v) return fail(FKL_ERR_TIMEOUT, "a bounded device wait gave up; outputs of that launch are incomplete");
+  return FKL_OK;
+}
 
 const char* fkl_version(void) { return "fkl-gb300 0.1 (sm_103a)"; }
 

@@ -226,14 +226,16 @@ FKL_D ChromaTerms chroma_terms(float uf, float vf) {
   t.bu = __fmul_rn(Bt601::cbu, uf);
   return t;
 }
-// RGB (0..255) of one luma sample yf = Y - 16 with its chroma terms.
-FKL_D F3 yuv_to_rgb(float yf, const ChromaTerms& t) {
+// BT.601 RGB of one luma sample yf = Y - 16 with its chroma terms, in
+// [0, 1]: each channel's saturating add is its clamp. The resampling read ops
+// interpolate these unit values and scale the result to 0..255 once per
+// output (scale255); interpolation and the scale commute in exact arithmetic.
+FKL_D F3 yuv_to_unit(float yf, const ChromaTerms& t) {
   const float l = __fmul_rn(Bt601::cy, yf);
-  F3 o;
-  o.v[0] = __fmul_rn(add_sat(l, t.rv), 255.f);
-  o.v[1] = __fmul_rn(sub_sat(l, t.guv), 255.f);
-  o.v[2] = __fmul_rn(add_sat(l, t.bu), 255.f);
-  return o;
+  return F3{{add_sat(l, t.rv), sub_sat(l, t.guv), add_sat(l, t.bu)}};
+}
+FKL_D F3 scale255(const F3& u) {
+  return F3{{__fmul_rn(u.v[0], 255.f), __fmul_rn(u.v[1], 255.f), __fmul_rn(u.v[2], 255.f)}};
 }
 
 constexpr float k2p23 = 8388608.f;
@@ -245,31 +247,32 @@ FKL_D float byte_as_float(uint32_t w, int k) {
   return __uint_as_float(__byte_perm(w, 0x4B000000u, 0x7440u | static_cast<uint32_t>(k)));
 }
 
-// yuv_to_rgb on a pair of luma samples (one per lane) with their chroma terms.
-FKL_D void rgb_pair(F2 yf, F2 cy, F2 rv, F2 guv, F2 bu, F2 c255, F2 (&o)[3]) {
+// yuv_to_unit on a pair of luma samples (one per lane) with their chroma terms.
+FKL_D void unit_pair(F2 yf, F2 cy, F2 rv, F2 guv, F2 bu, F2 (&o)[3]) {
   float l0, l1, r0, r1, g0, g1, b0, b1;
   f2split(f2mul(cy, yf), l0, l1);
   f2split(rv, r0, r1);
   f2split(guv, g0, g1);
   f2split(bu, b0, b1);
-  o[0] = f2mul(f2(add_sat(l0, r0), add_sat(l1, r1)), c255);
-  o[1] = f2mul(f2(sub_sat(l0, g0), sub_sat(l1, g1)), c255);
-  o[2] = f2mul(f2(add_sat(l0, b0), add_sat(l1, b1)), c255);
+  o[0] = f2(add_sat(l0, r0), add_sat(l1, r1));
+  o[1] = f2(sub_sat(l0, g0), sub_sat(l1, g1));
+  o[2] = f2(add_sat(l0, b0), add_sat(l1, b1));
 }
 
-// One decoded NV12 sample at absolute source coordinates (sx, sy): nearest
-// (co-sited) chroma sample (sx/2, sy/2), U then V.
-FKL_D F3 nv12_sample(const ResampleParams& p, int sx, int sy) {
+// One decoded NV12 sample in [0, 1] at absolute source coordinates (sx, sy):
+// nearest (co-sited) chroma sample (sx/2, sy/2), U then V.
+FKL_D F3 nv12_unit(const ResampleParams& p, int sx, int sy) {
   const float yf = static_cast<float>(__ldg(p.src + static_cast<int64_t>(sy) * p.pitch + sx)) - 16.f;
   const uint8_t* c = p.uv + static_cast<int64_t>(sy >> 1) * p.pitch + (sx & ~1);
   const float uf = static_cast<float>(__ldg(c)) - 128.f;
   const float vf = static_cast<float>(__ldg(c + 1)) - 128.f;
-  return yuv_to_rgb(yf, chroma_terms(uf, vf));
+  return yuv_to_unit(yf, chroma_terms(uf, vf));
 }
 
 // NV12 frame -> BT.601 RGB -> crop window -> bilinear resize -> placement.
 // Every tap is decoded (and clamped) first, then interpolated ("YUV->RGB,
-// then resize" order).
+// then resize" order); taps stay in [0, 1] and the interpolated value is
+// scaled to 0..255.
 struct ResizeNV12 {
   using InstanceType = ReadType;
   using ParamsType = ResampleParams;
@@ -280,11 +283,11 @@ struct ResizeNV12 {
     if (lx < 0 || ly < 0 || lx >= p.dw || ly >= p.dh) return F3{{p.pad, p.pad, p.pad}};
     const AxisTap tx = AxisWalker(lx, p.rw, p.dw).tap();
     const AxisTap ty = AxisWalker(ly, p.rh, p.dh).tap();
-    const F3 t00 = nv12_sample(p, p.rx + tx.i0, p.ry + ty.i0);
-    const F3 t01 = nv12_sample(p, p.rx + tx.i1, p.ry + ty.i0);
-    const F3 t10 = nv12_sample(p, p.rx + tx.i0, p.ry + ty.i1);
-    const F3 t11 = nv12_sample(p, p.rx + tx.i1, p.ry + ty.i1);
-    return blend_float(t00, t01, t10, t11, tx, 2 * p.dw, ty, 2 * p.dh);
+    const F3 t00 = nv12_unit(p, p.rx + tx.i0, p.ry + ty.i0);
+    const F3 t01 = nv12_unit(p, p.rx + tx.i1, p.ry + ty.i0);
+    const F3 t10 = nv12_unit(p, p.rx + tx.i0, p.ry + ty.i1);
+    const F3 t11 = nv12_unit(p, p.rx + tx.i1, p.ry + ty.i1);
+    return scale255(blend_float(t00, t01, t10, t11, tx, 2 * p.dw, ty, 2 * p.dh));
   }
 
   // Exact 2x downscale of an even-aligned window: output k of the span is
@@ -293,7 +296,11 @@ struct ResizeNV12 {
   // vectors. Outputs are processed in pairs, one per lane of the packed
   // f32x2 instructions; only the saturating adds are scalar. The result
   // equals exec() bit for bit: per lane the same IEEE operations run in the
-  // same order, and with weights 1/2 the blend is fl(fl(t00 + t10) + fl(t01 + t11)) / 4.
+  // same order. With weights 1/2 the blend of unit taps is exactly
+  // fl(fl(u00 + u10) + fl(u01 + u11)) / 4, and scaled by 255 that is
+  // fl(fl(fl(u00 + u10) + fl(u01 + u11)) * 63.75). No packed multiply feeds
+  // a packed add in this sequence, so nothing can be fused into a
+  // multiply-add that would round differently from the scalar form.
   template <int V>
   static FKL_D void span_fast2x(const ParamsType& p, int lx, int ly, F3 (&out)[V]) {
     static_assert(V % 8 == 0, "2x path reads 16-byte vectors");
@@ -309,9 +316,17 @@ struct ResizeNV12 {
       b[i] = __ldg(r1 + i);
       c[i] = __ldg(rc + i);
     }
+    compute2x<V>(a, b, c, out);
+  }
+
+  // The arithmetic of the 2x span from the 16-byte words of the two luma
+  // rows (a, b) and the chroma row (c), wherever they were loaded from.
+  template <int V>
+  static FKL_D void compute2x(const uint4 (&a)[V / 8], const uint4 (&b)[V / 8], const uint4 (&c)[V / 8],
+                              F3 (&out)[V]) {
     const F2 kY = f2s(k2p23 + 16.f), kC = f2s(k2p23 + 128.f);
     const F2 cy = f2s(Bt601::cy), crv = f2s(Bt601::crv), cgu = f2s(Bt601::cgu), cgv = f2s(Bt601::cgv),
-             cbu = f2s(Bt601::cbu), c255 = f2s(255.f), quarter = f2s(0.25f);
+             cbu = f2s(Bt601::cbu), c6375 = f2s(63.75f);
 #pragma unroll
     for (int k = 0; k < V; k += 2) {
       // outputs k, k+1 use bytes 2k .. 2k+3 of each row: word (k % 8) / 2 of
@@ -325,15 +340,15 @@ struct ResizeNV12 {
       const F2 v = f2sub(f2(byte_as_float(wc, 1), byte_as_float(wc, 3)), kC);
       const F2 rv = f2mul(crv, v), guv = f2fma(cgu, u, f2mul(cgv, v)), bu = f2mul(cbu, u);
       F2 t[4][3];  // taps row 0 left, row 0 right, row 1 left, row 1 right
-      rgb_pair(f2sub(f2(byte_as_float(wa, 0), byte_as_float(wa, 2)), kY), cy, rv, guv, bu, c255, t[0]);
-      rgb_pair(f2sub(f2(byte_as_float(wa, 1), byte_as_float(wa, 3)), kY), cy, rv, guv, bu, c255, t[1]);
-      rgb_pair(f2sub(f2(byte_as_float(wb, 0), byte_as_float(wb, 2)), kY), cy, rv, guv, bu, c255, t[2]);
-      rgb_pair(f2sub(f2(byte_as_float(wb, 1), byte_as_float(wb, 3)), kY), cy, rv, guv, bu, c255, t[3]);
+      unit_pair(f2sub(f2(byte_as_float(wa, 0), byte_as_float(wa, 2)), kY), cy, rv, guv, bu, t[0]);
+      unit_pair(f2sub(f2(byte_as_float(wa, 1), byte_as_float(wa, 3)), kY), cy, rv, guv, bu, t[1]);
+      unit_pair(f2sub(f2(byte_as_float(wb, 0), byte_as_float(wb, 2)), kY), cy, rv, guv, bu, t[2]);
+      unit_pair(f2sub(f2(byte_as_float(wb, 1), byte_as_float(wb, 3)), kY), cy, rv, guv, bu, t[3]);
 #pragma unroll
       for (int ch = 0; ch < 3; ++ch) {
         const F2 left = f2add(t[0][ch], t[2][ch]);
         const F2 right = f2add(t[1][ch], t[3][ch]);
-        f2split(f2mul(f2add(left, right), quarter), out[k].v[ch], out[k + 1].v[ch]);
+        f2split(f2mul(f2add(left, right), c6375), out[k].v[ch], out[k + 1].v[ch]);
       }
     }
   }
@@ -359,8 +374,9 @@ struct ResizeNV12 {
 
 // NV12 -> RGB -> exact 2x downscale (rw = 2 dw, rh = 2 dh) -> placement: a
 // specialisation of ResizeNV12 with no division in it. Every output is the
-// mean of one 2x2 block, fl(fl(t00 + t10) + fl(t01 + t11)) * 1/4, which is
-// what the general bilinear blend computes bit for bit when all weights are 1/2.
+// mean of one 2x2 block of unit taps scaled to 0..255,
+// fl(fl(fl(u00 + u10) + fl(u01 + u11)) * 63.75), which is what the general
+// bilinear blend and scale255 compute bit for bit when all weights are 1/2.
 struct ResizeNV12x2 {
   using InstanceType = ReadType;
   using ParamsType = ResampleParams;
@@ -370,14 +386,14 @@ struct ResizeNV12x2 {
     const int lx = pt.x - p.ox, ly = pt.y - p.oy;
     if (lx < 0 || ly < 0 || lx >= p.dw || ly >= p.dh) return F3{{p.pad, p.pad, p.pad}};
     const int sx = p.rx + 2 * lx, sy = p.ry + 2 * ly;
-    const F3 t00 = nv12_sample(p, sx, sy);
-    const F3 t01 = nv12_sample(p, sx + 1, sy);
-    const F3 t10 = nv12_sample(p, sx, sy + 1);
-    const F3 t11 = nv12_sample(p, sx + 1, sy + 1);
+    const F3 t00 = nv12_unit(p, sx, sy);
+    const F3 t01 = nv12_unit(p, sx + 1, sy);
+    const F3 t10 = nv12_unit(p, sx, sy + 1);
+    const F3 t11 = nv12_unit(p, sx + 1, sy + 1);
     F3 o;
 #pragma unroll
     for (int c = 0; c < 3; ++c)
-      o.v[c] = __fmul_rn(__fadd_rn(__fadd_rn(t00.v[c], t10.v[c]), __fadd_rn(t01.v[c], t11.v[c])), 0.25f);
+      o.v[c] = __fmul_rn(__fadd_rn(__fadd_rn(t00.v[c], t10.v[c]), __fadd_rn(t01.v[c], t11.v[c])), 63.75f);
     return o;
   }
 
@@ -400,19 +416,21 @@ struct ResizeNV12x2 {
   }
 };
 
-// NV12 decode at full resolution (the first kernel of the unfused NV12 chain).
+// NV12 decode at full resolution to unit-range RGB (the first kernel of the
+// unfused NV12 chain; its resize kernel scales to 0..255).
 struct DecodeNV12 {
   using InstanceType = ReadType;
   using ParamsType = ResampleParams;
   using OutputType = F3;
-  static FKL_D F3 exec(const Point& pt, const ParamsType& p) {
-    return nv12_sample(p, p.rx + pt.x, p.ry + pt.y);
-  }
+  static FKL_D F3 exec(const Point& pt, const ParamsType& p) { return nv12_unit(p, p.rx + pt.x, p.ry + pt.y); }
 };
 
 // Packed float32 3-channel image (an intermediate of the unfused chains),
-// read through the same resampling geometry with float taps.
-struct ResizeF32C3 {
+// read through the same resampling geometry with float taps. kUnit: the
+// image holds unit-range RGB (the unfused NV12 decode) and the blend is scaled
+// to 0..255, the rounding points of the fused NV12 read.
+template <bool kUnit>
+struct ResizeF32C3T {
   using InstanceType = ReadType;
   using ParamsType = ResampleParams;
   using OutputType = F3;
@@ -425,11 +443,14 @@ struct ResizeF32C3 {
     if (lx < 0 || ly < 0 || lx >= p.dw || ly >= p.dh) return F3{{p.pad, p.pad, p.pad}};
     const AxisTap tx = AxisWalker(lx, p.rw, p.dw).tap();
     const AxisTap ty = AxisWalker(ly, p.rh, p.dh).tap();
-    return blend_float(load(p, p.rx + tx.i0, p.ry + ty.i0), load(p, p.rx + tx.i1, p.ry + ty.i0),
-                       load(p, p.rx + tx.i0, p.ry + ty.i1), load(p, p.rx + tx.i1, p.ry + ty.i1),
-                       tx, 2 * p.dw, ty, 2 * p.dh);
+    const F3 b = blend_float(load(p, p.rx + tx.i0, p.ry + ty.i0), load(p, p.rx + tx.i1, p.ry + ty.i0),
+                             load(p, p.rx + tx.i0, p.ry + ty.i1), load(p, p.rx + tx.i1, p.ry + ty.i1), tx,
+                             2 * p.dw, ty, 2 * p.dh);
+    if constexpr (kUnit) return scale255(b);
+    return b;
   }
 };
+using ResizeF32C3 = ResizeF32C3T<false>;
 
 // Packed float32 3-channel image, pixel for pixel (unfused per-op kernels).
 struct ReadF32C3 {
@@ -543,8 +564,18 @@ struct Sub3 {
   static FKL_D F3 exec(const F3& x, const ParamsType& p) {
     return F3{{__fsub_rn(x.v[0], p.c[0]), __fsub_rn(x.v[1], p.c[1]), __fsub_rn(x.v[2], p.c[2])}};
   }
+  // Per lane (scalar sub.rn): a packed subtract of the product of a packed
+  // multiply (Mul3 before it) can be fused into one multiply-add by the
+  // assembler, which would round once where the two ops round twice.
   static FKL_D F3x2 exec_pair(const F3x2& x, const ParamsType& p) {
-    return F3x2{{f2sub(x.v[0], f2s(p.c[0])), f2sub(x.v[1], f2s(p.c[1])), f2sub(x.v[2], f2s(p.c[2]))}};
+    F3x2 o;
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+      float a, b;
+      f2split(x.v[c], a, b);
+      o.v[c] = f2(__fsub_rn(a, p.c[c]), __fsub_rn(b, p.c[c]));
+    }
+    return o;
   }
 };
 // IEEE division. `on` = 0 passes the value through untouched (a chain

@@ -5,7 +5,11 @@
 #pragma once
 
 #include <cstring>
+#include <map>
+#include <mutex>
+#include <tuple>
 
+#include "fkl/staged.cuh"
 #include "registry.h"
 
 namespace fkl_impl {
@@ -101,8 +105,104 @@ cudaError_t run_float_chain(const LaunchCtx& c) {
   return run_float_chain_cap<ROp, OutT, kSplit, kSwap, kTail, V, RY, kBatchCap>(c);
 }
 
+// Row-staged launch (shape.ry <= 0, shape.ty = output rows per job) of the
+// exact-2x NV12 read: a persistent grid of min(jobs, SMs x resident CTAs)
+// CTAs of shape.tx threads with a ring of -shape.ry stages (shape.ry == 0:
+// as many as fill about kStageBudget bytes, 2..kMaxStages).
+constexpr int kStageBudget = 64 * 1024;
+constexpr int kStagedSmemMax = 200 * 1024;
+
+inline int staged_stages(const fkl_launch_shape& sh, int stage_bytes) {
+  if (sh.ry < 0) return -sh.ry;
+  return std::max(2, std::min(fkl::kMaxStages, kStageBudget / std::max(stage_bytes, 1)));
+}
+
+template <class OutT, bool kSwap, int kTail, int V>
+cudaError_t run_staged(const LaunchCtx& c) {
+  using RB = fkl::BatchRead<fkl::ResizeNV12x2, kBatchCap>;
+  using W = fkl::WriteSplit<OutT>;
+  const Spec& s = *c.spec;
+  auto tail = make_tail<kTail>(s);
+  auto cops = [&] {
+    if constexpr (kSwap) {
+      return fkl::prepend(fkl::IOp<fkl::SwapRB<fkl::F3>>{}, tail);
+    } else {
+      return tail;
+    }
+  }();
+  using Cops = decltype(cops);
+  fkl::StagedArgs<RB, W, Cops> a;
+  std::memset(&a.rp, 0, sizeof(a.rp));
+  a.rp.count = c.n;
+  std::memcpy(a.rp.p, c.imgs, sizeof(fkl::ResampleParams) * c.n);
+  a.wp = c.out;
+  a.cops = cops;
+  a.H = c.H;
+  a.W_ = c.W;
+  a.R = c.shape.ty;
+  a.row_bytes = 2 * c.W;
+  const int stage_bytes = 3 * a.R * a.row_bytes;
+  a.stages = staged_stages(c.shape, stage_bytes);
+  a.jobs_per_image = (c.H + a.R - 1) / a.R;
+  a.jobs = c.n * a.jobs_per_image;
+  a.error = c.device_error;
+  const int smem = a.stages * stage_bytes;
+  if (a.jobs == 0) return cudaSuccess;
+
+  auto kernel = fkl::staged_nv12x2_kernel<V, RB, W, Cops>;
+  // per (device, threads, shared bytes): resident CTAs per SM, after the
+  // kernel's shared-memory limit has been raised once on that device
+  static std::mutex mu;
+  static std::map<std::tuple<int, int, int>, int> resident;
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  int per_sm = 0;
+  {
+    std::lock_guard<std::mutex> lk(mu);
+    const auto key = std::make_tuple(dev, c.shape.tx, smem);
+    auto it = resident.find(key);
+    if (it == resident.end()) {
+      e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, kStagedSmemMax);
+      if (e != cudaSuccess) return e;
+      e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, c.shape.tx, smem);
+      if (e != cudaSuccess) return e;
+      if (per_sm < 1) return cudaErrorInvalidConfiguration;
+      resident.emplace(key, per_sm);
+    } else {
+      per_sm = it->second;
+    }
+  }
+  const int grid = std::min(a.jobs, sm_count() * per_sm);
+  kernel<<<grid, c.shape.tx, smem, c.stream>>>(a);
+  return cudaGetLastError();
+}
+
+// Whether the row-staged kernel can run this launch (its preconditions).
+inline bool staged_eligible(const LaunchCtx& c, int V) {
+  if (!c.all_exact2x || !c.device_error || c.W % V || (2 * c.W) % 16) return false;
+  if (c.shape.ty < 1 || c.shape.tx < 32 || c.shape.tx > 256 || c.shape.tx % 32) return false;
+  const int stage_bytes = 3 * c.shape.ty * 2 * c.W;
+  const int stages = staged_stages(c.shape, stage_bytes);
+  if (stages < 2 || stages > fkl::kMaxStages || int64_t(stages) * stage_bytes > kStagedSmemMax) return false;
+  for (int i = 0; i < c.n; ++i) {
+    const auto& p = c.imgs[i];
+    if (!(p.flags & fkl::kFast2x) || p.ox != 0 || p.dw != c.W) return false;
+  }
+  return true;
+}
+
 template <class ROp, class OutT, bool kSplit, bool kSwap, int kTail, int V>
 cudaError_t float_by_ry(const LaunchCtx& c) {
+  if (c.shape.ry <= 0) {
+    if constexpr (std::is_same_v<ROp, fkl::ResizeNV12x2> && kSplit && V % 8 == 0) {
+      if (staged_eligible(c, V)) return run_staged<OutT, kSwap, kTail, V>(c);
+    }
+    // not eligible: the register kernel with a fixed block
+    LaunchCtx d = c;
+    d.shape = fkl_launch_shape{V, 32, 8, 1};
+    return run_float_chain<ROp, OutT, kSplit, kSwap, kTail, V, 1>(d);
+  }
   if (c.shape.ry == 1) return run_float_chain<ROp, OutT, kSplit, kSwap, kTail, V, 1>(c);
   if constexpr (V <= 8) {  // two rows of 16 pixels would not fit in registers
     if (c.shape.ry == 2) return run_float_chain<ROp, OutT, kSplit, kSwap, kTail, V, 2>(c);

@@ -137,7 +137,8 @@ cudaError_t launch_unfused_image(const Spec& s, const fkl::ResampleParams& img,
     return float_tail(s, ws0, ws1, o, H, W, st);
   }
   if (s.family == FAM_NV12) {
-    // decode the source window to RGB f32 HWC, resize / letterbox it, ...
+    // decode the source window to unit-range RGB f32 HWC, resize / letterbox
+    // it (scaled to 0..255 after the blend), ...
     fkl::ResampleParams dec = img;
     e = step<fkl::DecodeNV12, PackF32>(dec, f32_out(ws0, img.rh, img.rw), fkl::make_tuple(), img.rh,
                                        img.rw, st);
@@ -148,7 +149,7 @@ cudaError_t launch_unfused_image(const Spec& s, const fkl::ResampleParams& img,
     rs.pitch = img.rw * 12;
     rs.rx = rs.ry = 0;
     rs.flags = 0;
-    e = step<fkl::ResizeF32C3, PackF32>(rs, f32_out(ws1, H, W), fkl::make_tuple(), H, W, st);
+    e = step<fkl::ResizeF32C3T<true>, PackF32>(rs, f32_out(ws1, H, W), fkl::make_tuple(), H, W, st);
     if (e != cudaSuccess) return e;
     return float_tail(s, ws1, ws0, o, H, W, st);
   }

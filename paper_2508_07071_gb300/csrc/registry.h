@@ -49,7 +49,11 @@ struct LaunchCtx {
   int H, W;
   cudaStream_t stream;
   bool all_exact2x;  // every image of the launch is an exact 2x downscale
+  int* device_error = nullptr;  // flag a bounded device wait sets when it gives up
 };
+
+// Device address of this library's wait-timeout flag on the current device.
+cudaError_t device_error_flag(int** out);
 
 // Fused launches of the float image families, one translation unit per
 // (source, output type): k_<src>_<type>.cu.

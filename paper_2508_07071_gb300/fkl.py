@@ -153,6 +153,7 @@ EXPORTS = {
     "fkl_execute_batch_scaled": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int32, ctypes.POINTER(fkl_tensor),
                                                 ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(fkl_tensor),
                                                 ctypes.c_void_p, ctypes.c_void_p]),
+    "fkl_device_check": (ctypes.c_int, []),
     "fkl_version": (ctypes.c_char_p, []),
 }
 
@@ -384,6 +385,11 @@ def fkl_last_error() -> str:
 
 def fkl_version() -> str:
     return _lib.fkl_version().decode()
+
+
+def fkl_device_check() -> None:
+    """Raises FklError(FKL_ERR_TIMEOUT) if a bounded device wait gave up."""
+    _check(_lib.fkl_device_check())
 
 
 def fkl_pipeline_kernel_name(p: int) -> str:

@@ -113,7 +113,16 @@ def test_launch_shapes(F):
         assert len(shapes) > 10
         assert F.fkl_pipeline_get_shape(p) in shapes
         for s in shapes:
-            assert s[0] in (4, 8, 16) and s[1] * s[2] <= 256 and s[3] in (1, 2)
+            if s[3] <= 0:  # row-staged kernel: tx threads, ty output rows per job, -ry stages
+                assert s[0] in (8, 16) and s[1] in (128, 256) and 1 <= s[2] <= 16 and 0 <= -s[3] <= 8
+            else:
+                assert s[0] in (4, 8, 16) and s[1] * s[2] <= 256 and s[3] in (1, 2)
+        assert any(s[3] <= 0 for s in shapes)
+        packed = F.fkl_pipeline_create(W.normalize_chain(224, 224, F.FKL_BF16))
+        try:
+            assert all(s[3] > 0 for s in F.fkl_pipeline_shapes(packed))
+        finally:
+            F.fkl_pipeline_destroy(packed)
         F.fkl_pipeline_set_shape(p, shapes[-1])
         assert F.fkl_pipeline_get_shape(p) == shapes[-1]
         with pytest.raises(F.FklError):

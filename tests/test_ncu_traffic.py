@@ -1,0 +1,41 @@
+"""The ncu launch-list reader that records per-launch DRAM traffic."""
+import json
+
+from paper_2508_07071_gb300 import ncu_traffic as T
+
+HEAD = ('"ID","Process ID","Process Name","Host Name","Kernel Name","Context","Stream","Block Size",'
+        '"Grid Size","Device","CC","Section Name","Metric Name","Metric Unit","Metric Value"\n')
+
+
+def row(i, kernel, metric, unit, value):
+    return (f'"{i}","1","python3","h","{kernel}","1","7","(8, 16, 1)","(5, 40, 256)","0","10.3",'
+            f'"Command line profiler metrics","{metric}","{unit}","{value}"\n')
+
+
+def test_parse_and_summarise(tmp_path):
+    lines = ["==PROF== Connected to process 1\n", HEAD]
+    for i, (rd, wr, t) in enumerate([(100, 50, 2000), (300, 150, 4000)]):
+        k = "void transform2d_kernel<16, 1, X>(Args2D<T3, T4, T5>)"
+        lines += [row(i, k, "dram__bytes_read.sum", "byte", rd), row(i, k, "dram__bytes_write.sum", "byte", wr),
+                  row(i, k, "gpu__time_duration.sum", "ns", f"{t:,}")]
+    lines += [row(2, "void other_kernel()", "dram__bytes_read.sum", "byte", 9),
+              row(2, "void other_kernel()", "dram__bytes_write.sum", "byte", 9),
+              row(2, "void other_kernel()", "gpu__time_duration.sum", "ns", 9)]
+    p = tmp_path / "l.csv"
+    p.write_text("".join(lines))
+    s = T.summarise(T.parse_launches(str(p), "transform2d"))
+    assert s == {"dram_bytes_per_launch": 300, "dram_read_bytes": 200, "dram_write_bytes": 100,
+                 "launches": 2, "mean_time_us_cold_serialised": 3.0}
+
+
+def test_source_hash_is_stable_and_short():
+    a, b = T.source_hash(), T.source_hash()
+    assert a == b and len(a) == 16 and int(a, 16) >= 0
+
+
+def test_committed_traffic_file_is_well_formed():
+    d = json.load(open(T.TRAFFIC))
+    for key, e in d.items():
+        # the total and the parts are rounded separately
+        assert abs(e["dram_bytes_per_launch"] - e["dram_read_bytes"] - e["dram_write_bytes"]) <= 2, key
+        assert len(e["source_hash"]) == 16 and e["command"].startswith("ncu ")

@@ -313,7 +313,7 @@ def test_unfused_equals_fused_bitwise(F, W):
     assert torch.equal(a.view(torch.int32), b.view(torch.int32))
 
     frames = synth.nv12_frames(3, 2, 720, 1280)
-    for fmt in ["bf16", "e4m3"]:
+    for fmt in ["f32", "f16", "bf16", "e4m3"]:
         a, _ = nv12_case(F, W, fmt, frames)
         b, _ = nv12_case(F, W, fmt, frames, unfused=True)
         assert torch.equal(a.view(torch.uint8), b.view(torch.uint8)), fmt
@@ -332,6 +332,25 @@ def test_unfused_equals_fused_bitwise(F, W):
     F.fkl_execute_batch_unfused(p.handle, [F.as_fkl(x)], None, F.as_fkl(y2), 0, 0)
     torch.cuda.synchronize()
     assert torch.equal(y1.view(torch.int32), y2.view(torch.int32))
+
+
+@pytest.mark.parametrize("src", ["packed", "nv12"])
+def test_mul_sub_pair_chain_equals_unfused_bitwise(F, W, src):
+    """A chain without Div runs its compute ops on packed pixel pairs; each op
+    still rounds on its own, as in the one-kernel-per-op form."""
+    if src == "packed":
+        img = torch.from_numpy(synth.packed_image(21, 90, 131)).cuda()
+        ops = [F.read_u8c3(), F.resize(64, 45), F.swap_rb(), F.mul(W.INV255), F.sub(W.IMAGENET_MEAN),
+               F.write_split(F.FKL_F32)]
+        srcs, layout = [img, img], None
+        rois = np.array([[0, 0, 131, 90], [3, 5, 101, 77]], np.int32)
+    else:
+        fr = torch.from_numpy(synth.nv12_frames(21, 2, 90, 128)).cuda()
+        ops = [F.read_nv12(), F.resize(64, 45), F.mul(W.INV255), F.sub(W.IMAGENET_MEAN), F.write_split(F.FKL_F32)]
+        srcs, layout, rois = [fr[0], fr[1]], F.FKL_LAYOUT_NV12, None
+    a = run_batch(F, ops, srcs, rois, (2, 3, 45, 64), "f32", layout_in=layout)
+    b = run_batch(F, ops, srcs, rois, (2, 3, 45, 64), "f32", layout_in=layout, unfused=True)
+    assert torch.equal(a.view(torch.int32), b.view(torch.int32))
 
 
 def test_every_launch_shape_gives_the_same_bytes(F, W):
@@ -529,3 +548,75 @@ def test_nv12_full_batch_autotuned_sampled(F, W, fmt):
     for i in [0, 100, cfg["n"] - 1]:
         want = O.preprocess_nv12(frames[i], 640, 640, pad=114.0, mul=1 / 255)
         check_output(out[i], want, fmt, scale, f"{fmt} frame {i} shape {best}")
+
+
+# ------------------------------------------------------------------ row-staged NV12 kernel (bulk copies into shared memory)
+
+def _staged_shapes(F, p):
+    return [s for s in F.fkl_pipeline_shapes(p.handle) if s[3] <= 0]
+
+
+@pytest.mark.parametrize("fmt", ["bf16", "e4m3", "f16", "f32"])
+@pytest.mark.parametrize("hw,out_wh", [
+    ((720, 1280), (640, 640)),   # letterbox: band rows above and below
+    ((720, 1280), (640, 600)),   # 600 rows: the last job of every image is ragged
+    ((80, 80), (40, 40)),        # width 40: V = 16 does not divide it (register kernel)
+])
+def test_every_nv12_launch_shape_gives_the_same_bytes(F, W, fmt, hw, out_wh):
+    """Scalar (V=4), vector and row-staged launches of one chain agree bit for bit."""
+    frames = synth.nv12_frames(11, 3, *hw)
+    dev = torch.from_numpy(frames).cuda()
+    ow, oh = out_wh
+    ops = [F.read_nv12(), F.letterbox(ow, oh, 114.0), F.mul(W.INV255),
+           F.write_split(code(F, fmt), W.E4M3_SCALE if fmt == "e4m3" else None)]
+    srcs = [dev[i] for i in range(3)]
+    base = run_batch(F, ops, srcs, None, (3, 3, oh, ow), fmt, layout_in=F.FKL_LAYOUT_NV12)
+    p = F.Pipeline(ops)
+    assert _staged_shapes(F, p), "row-staged shapes are listed for NV12 split outputs"
+    for shape in F.fkl_pipeline_shapes(p.handle):
+        got = run_batch(F, ops, srcs, None, (3, 3, oh, ow), fmt, layout_in=F.FKL_LAYOUT_NV12, shape=shape)
+        assert torch.equal(got.view(torch.uint8), base.view(torch.uint8)), shape
+    F.fkl_device_check()
+    scale = W.E4M3_SCALE if fmt == "e4m3" else 1.0
+    rgb = O.nv12_to_rgb(frames[2])
+    want = O.split(O.multiply(O.letterbox(rgb, ow, oh, 114.0), 1 / 255))
+    check_output(got[2], want, fmt, scale, f"staged {fmt} {hw}->{out_wh}")
+
+
+def test_row_staged_kernel_many_images_and_normalise(F, W):
+    """300 images (two launches of the 256-entry parameter table), swap + normalise tail."""
+    n = 300
+    frames = synth.nv12_frames(12, n, 64, 128)
+    dev = torch.from_numpy(frames).cuda()
+    ops = [F.read_nv12(), F.resize(64, 32), F.swap_rb(), F.mul(W.INV255), F.sub(W.IMAGENET_MEAN),
+           F.div(W.IMAGENET_STD), F.write_split(F.FKL_F16)]
+    srcs = [dev[i] for i in range(n)]
+    base = run_batch(F, ops, srcs, None, (n, 3, 32, 64), "f16", layout_in=F.FKL_LAYOUT_NV12)
+    p = F.Pipeline(ops)
+    for shape in _staged_shapes(F, p):
+        got = run_batch(F, ops, srcs, None, (n, 3, 32, 64), "f16", layout_in=F.FKL_LAYOUT_NV12, shape=shape)
+        assert torch.equal(got.view(torch.int16), base.view(torch.int16)), shape
+    F.fkl_device_check()
+    for i in [0, 255, 256, n - 1]:
+        t = O.swap_rb(O.resize_bilinear(O.nv12_to_rgb(frames[i]), 64, 32))
+        want = O.split(O.divide(O.subtract(O.multiply(t, 1 / 255), W.IMAGENET_MEAN), W.IMAGENET_STD))
+        check_output(got[i], want, "f16", 1.0, f"staged normalise image {i}")
+
+
+def test_row_staged_shape_falls_back_on_unaligned_crops(F, W):
+    """A crop whose x offset is not a multiple of 16 makes the batch ineligible."""
+    frames = synth.nv12_frames(13, 2, 96, 160)
+    dev = torch.from_numpy(frames).cuda()
+    ops = [F.read_nv12(), F.resize(64, 32), F.mul(W.INV255), F.write_split(F.FKL_BF16)]
+    rois = np.array([[8, 4, 128, 64], [16, 2, 128, 64]], np.int32)
+    srcs = [dev[0], dev[1]]
+    base = run_batch(F, ops, srcs, rois, (2, 3, 32, 64), "bf16", layout_in=F.FKL_LAYOUT_NV12)
+    p = F.Pipeline(ops)
+    for shape in _staged_shapes(F, p):
+        got = run_batch(F, ops, srcs, rois, (2, 3, 32, 64), "bf16", layout_in=F.FKL_LAYOUT_NV12, shape=shape)
+        assert torch.equal(got.view(torch.int16), base.view(torch.int16)), shape
+    F.fkl_device_check()
+    for i in range(2):
+        x, y, w, h = rois[i]
+        t = O.resize_bilinear(O.nv12_to_rgb(frames[i])[y:y + h, x:x + w], 64, 32)
+        check_output(got[i], O.split(O.multiply(t, 1 / 255)), "bf16", 1.0, f"fallback image {i}")
