@@ -458,11 +458,21 @@ FKL_API fkl_status fkl_pipeline_autotune_ex(fkl_pipeline p, int32_t n, const fkl
 
 /* Reads and clears the flag the fused kernels' bounded device waits set when
  * one gives up (the row-staged NV12 kernel waits on its own copies; a wait
- * longer than 1 s stops that CTA, whose outputs are then incomplete).
+ * longer than the limit, 1 s by default, stops that CTA, whose outputs are
+ * then incomplete).
  * Synchronises the current device first. Returns FKL_ERR_TIMEOUT if the flag
  * was set since the last call on this device, FKL_OK if not, FKL_ERR_CUDA if a
  * CUDA call failed (the message has it). */
 FKL_API fkl_status fkl_device_check(void);
+
+/* Limit of one bounded device wait of the fused kernels, for launches made
+ * after the call (process-wide). 0 restores the default of 1 s; at most
+ * 10 s (FKL_ERR_INVALID above); below 1 us (the device timer's resolution) a
+ * wait gives up unless its phase is complete at the first poll. A wait that runs out sets the flag
+ * fkl_device_check reads; the kernel still lets its own copies in flight land
+ * (a separate, fixed 1 s bound) before it leaves, so a short limit ends work
+ * early but leaves the device usable. */
+FKL_API fkl_status fkl_set_device_wait_limit(uint64_t ns);
 
 /* Library version string. */
 FKL_API const char* fkl_version(void);

@@ -5,6 +5,7 @@
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
+#include <atomic>
 #include <mutex>
 #include <new>
 #include <string>
@@ -345,6 +346,14 @@ static __device__ __align__(256) uint8_t g_unfused_scratch[kStaticScratchBytes];
 static __device__ int g_device_error;
 
 namespace {
+constexpr unsigned long long kDefaultWaitNs = 1000ull * 1000 * 1000;  // 1 s
+constexpr unsigned long long kMaxWaitNs = 10ull * kDefaultWaitNs;
+std::atomic<unsigned long long> g_wait_ns{kDefaultWaitNs};
+}  // namespace
+
+unsigned long long device_wait_limit_ns() { return g_wait_ns.load(std::memory_order_relaxed); }
+
+namespace {
 std::mutex g_scratch_mu;
 void* g_error_ptr[64] = {nullptr};
 void* g_scratch_ptr[64] = {nullptr};
@@ -543,6 +552,7 @@ fkl_status execute_batch_impl(fkl_pipeline p, int32_t n, const fkl_tensor* ins, 
     c.all_exact2x = true;
     for (int i = 0; i < c.n; ++i) c.all_exact2x = c.all_exact2x && (c.imgs[i].flags & fkl::kExact2x);
     c.device_error = err_flag;
+    c.wait_ns = device_wait_limit_ns();
     const cudaError_t e = launch_family(c);
     if (e != cudaSuccess) return cuda_fail(e, "fused kernel launch");
   }
@@ -576,6 +586,12 @@ fkl_status fkl_pipeline_create(const fkl_op_desc* ops, int32_t n_ops, fkl_pipeli
 void fkl_pipeline_destroy(fkl_pipeline p) { delete p; }
 
 const char* fkl_last_error(void) { return t_error.c_str(); }
+
+fkl_status fkl_set_device_wait_limit(uint64_t ns) {
+  if (ns > kMaxWaitNs) return fail(FKL_ERR_INVALID, "wait limit above 10 s");
+  g_wait_ns.store(ns ? ns : kDefaultWaitNs, std::memory_order_relaxed);
+  return FKL_OK;
+}
 
 fkl_status fkl_device_check(void) {
   int* flag = nullptr;

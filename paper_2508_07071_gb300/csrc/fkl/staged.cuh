@@ -7,9 +7,10 @@
 // flight. The arithmetic is ResizeNV12::compute2x, the same as the
 // register-load path, so both give the same bits.
 //
-// Every wait is bounded by the global timer: a wait that runs out records a
-// timeout in a device flag (read by the host through the C ABI), lets the
-// CTA's copies in flight land (again bounded) and leaves the kernel.
+// Every wait is bounded by the global timer: a wait that runs out (after
+// `wait_ns`, 1 s unless the host set another limit) records a timeout in a
+// device flag (read by the host through the C ABI), lets the CTA's copies in
+// flight land (a separate, fixed 1 s bound) and leaves the kernel.
 #pragma once
 
 #include "ops.cuh"
@@ -34,6 +35,15 @@ FKL_D bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
       : "memory");
   return ok != 0;
 }
+FKL_D bool mbar_test_wait(uint64_t* bar, uint32_t parity) {  // non-blocking poll
+  uint32_t ok;
+  asm volatile(
+      "{\n .reg .pred p;\n mbarrier.test_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}"
+      : "=r"(ok)
+      : "r"(smem_u32(bar)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
 // 1-D bulk copy global -> shared; 16-byte aligned addresses, size a multiple of 16.
 FKL_D void bulk_load(void* dst, const void* src, uint32_t bytes, uint64_t* bar) {
   asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
@@ -48,7 +58,9 @@ FKL_D unsigned long long now_ns() {
   return t;
 }
 
-constexpr unsigned long long kStagedWaitNs = 1000ull * 1000 * 1000;  // 1 s per wait
+// Limit of the wait that lets a CTA's copies in flight land before it leaves
+// after a timeout; fixed, whatever the consumer-wait limit is.
+constexpr unsigned long long kStagedDrainNs = 1000ull * 1000 * 1000;  // 1 s
 constexpr int kMaxStages = 8;
 
 template <class RB, class W, class Cops>
@@ -63,13 +75,19 @@ struct StagedArgs {
   int32_t jobs_per_image;  // ceil(H / R)
   int32_t jobs;            // images x jobs_per_image
   int* error;              // device flag, set to 1 when a wait gives up
+  unsigned long long wait_ns;  // limit of one consumer wait on a stage
 };
 
-// Bounded wait on `bar` for `parity`; false when it gave up.
-FKL_D bool staged_wait(uint64_t* bar, uint32_t parity) {
+// Bounded wait on `bar` for `parity`; false when it gave up after limit_ns.
+// try_wait may itself suspend the thread for a while, so the phase is first
+// polled without blocking; a limit below the global timer's 1 us resolution
+// allows that one poll only.
+FKL_D bool staged_wait(uint64_t* bar, uint32_t parity, unsigned long long limit_ns) {
+  if (mbar_test_wait(bar, parity)) return true;
+  if (limit_ns < 1000) return false;
   const unsigned long long t0 = now_ns();
   while (!mbar_try_wait(bar, parity)) {
-    if (now_ns() - t0 > kStagedWaitNs) return false;
+    if (now_ns() - t0 > limit_ns) return false;
   }
   return true;
 }
@@ -134,7 +152,7 @@ __global__ void __launch_bounds__(256) staged_nv12x2_kernel(const __grid_constan
     const int s = i % S;
     // every thread waits (the acquire of the copied bytes); the CTA leaves
     // together if any of them gave up
-    if (!__syncthreads_and(staged_wait(&bars[s], (i / S) & 1))) {
+    if (!__syncthreads_and(staged_wait(&bars[s], (i / S) & 1, a.wait_ns))) {
       ok = false;
       break;
     }
@@ -191,7 +209,7 @@ __global__ void __launch_bounds__(256) staged_nv12x2_kernel(const __grid_constan
     // let the copies still in flight land before the CTA's shared memory is released
     for (int k = 0; k < S; ++k) {
       const int ii = i + k;
-      if (blockIdx.x + ii * gridDim.x < a.jobs) staged_wait(&bars[ii % S], (ii / S) & 1);
+      if (blockIdx.x + ii * gridDim.x < a.jobs) staged_wait(&bars[ii % S], (ii / S) & 1, kStagedDrainNs);
     }
   }
 }

@@ -146,6 +146,7 @@ cudaError_t run_staged(const LaunchCtx& c) {
   a.jobs_per_image = (c.H + a.R - 1) / a.R;
   a.jobs = c.n * a.jobs_per_image;
   a.error = c.device_error;
+  a.wait_ns = c.wait_ns ? c.wait_ns : 1000000000ull;
   const int smem = a.stages * stage_bytes;
   if (a.jobs == 0) return cudaSuccess;
 

@@ -50,7 +50,11 @@ struct LaunchCtx {
   cudaStream_t stream;
   bool all_exact2x;  // every image of the launch is an exact 2x downscale
   int* device_error = nullptr;  // flag a bounded device wait sets when it gives up
+  unsigned long long wait_ns = 0;  // limit of one bounded device wait
 };
+
+// Limit of one bounded device wait of the fused kernels (fkl_set_device_wait_limit).
+unsigned long long device_wait_limit_ns();
 
 // Device address of this library's wait-timeout flag on the current device.
 cudaError_t device_error_flag(int** out);

@@ -154,6 +154,7 @@ EXPORTS = {
                                                 ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(fkl_tensor),
                                                 ctypes.c_void_p, ctypes.c_void_p]),
     "fkl_device_check": (ctypes.c_int, []),
+    "fkl_set_device_wait_limit": (ctypes.c_int, [ctypes.c_uint64]),
     "fkl_version": (ctypes.c_char_p, []),
 }
 
@@ -390,6 +391,11 @@ def fkl_version() -> str:
 def fkl_device_check() -> None:
     """Raises FklError(FKL_ERR_TIMEOUT) if a bounded device wait gave up."""
     _check(_lib.fkl_device_check())
+
+
+def fkl_set_device_wait_limit(ns: int) -> None:
+    """Limit of one bounded device wait (0: the default, 1 s)."""
+    _check(_lib.fkl_set_device_wait_limit(int(ns)))
 
 
 def fkl_pipeline_kernel_name(p: int) -> str:

@@ -204,3 +204,11 @@ def test_unfused_workspace_size_is_the_memory_saved(F):
         assert 60 * 120 * 12 == 86400 and 3 * 86400 == 259200
     finally:
         F.fkl_pipeline_destroy(p)
+
+
+def test_device_wait_limit_is_validated_on_the_host(F):
+    with pytest.raises(F.FklError) as e:
+        F.fkl_set_device_wait_limit(11 * 10**9)
+    assert e.value.status == F.FKL_ERR_INVALID
+    F.fkl_set_device_wait_limit(5 * 10**8)
+    F.fkl_set_device_wait_limit(0)  # back to the default

@@ -620,3 +620,27 @@ def test_row_staged_shape_falls_back_on_unaligned_crops(F, W):
         x, y, w, h = rois[i]
         t = O.resize_bilinear(O.nv12_to_rgb(frames[i])[y:y + h, x:x + w], 64, 32)
         check_output(got[i], O.split(O.multiply(t, 1 / 255)), "bf16", 1.0, f"fallback image {i}")
+
+
+def test_row_staged_wait_limit_reports_timeout_and_device_stays_usable(F, W):
+    """A consumer wait that runs out sets the device flag; the kernel drains
+    its own copies and leaves, and the next launch is whole again."""
+    frames = synth.nv12_frames(14, 64, 720, 1280)
+    dev = torch.from_numpy(frames).cuda()
+    ops = W.nv12_letterbox_chain(F.FKL_BF16)
+    srcs = [dev[i] for i in range(64)]
+    base = run_batch(F, ops, srcs, None, (64, 3, 640, 640), "bf16", layout_in=F.FKL_LAYOUT_NV12)
+    F.fkl_device_check()
+    shape = (8, 128, 4, -2)
+    try:
+        F.fkl_set_device_wait_limit(1)  # 1 ns: every wait that has to wait at all gives up
+        run_batch(F, ops, srcs, None, (64, 3, 640, 640), "bf16", layout_in=F.FKL_LAYOUT_NV12, shape=shape)
+        with pytest.raises(F.FklError) as e:
+            F.fkl_device_check()
+        assert e.value.status == F.FKL_ERR_TIMEOUT
+    finally:
+        F.fkl_set_device_wait_limit(0)
+    F.fkl_device_check()  # cleared by the previous call
+    got = run_batch(F, ops, srcs, None, (64, 3, 640, 640), "bf16", layout_in=F.FKL_LAYOUT_NV12, shape=shape)
+    F.fkl_device_check()
+    assert torch.equal(got.view(torch.int16), base.view(torch.int16))
