@@ -29,21 +29,14 @@ if ROOT not in sys.path:
 METRIC = "Fused GB/s vs 8 TB/s HBM & speedup over unfused per-op kernels, same GB300"
 
 
-def kernel_source_hash() -> str:
-    """Hash of the kernel sources and build flags: a stored ncu traffic
-    figure applies only to the kernel build it was measured on."""
-    from paper_2508_07071_gb300.ncu_traffic import source_hash
-    return source_hash()
-
-
 def measured_traffic(key: str):
     """DRAM bytes per launch (read + write) from the committed ncu summary,
-    or None when the kernel sources changed since it was taken."""
-    path = os.path.join(ROOT, "profiles", "traffic.json")
-    if not os.path.exists(path):
+    or None when the kernel's sources or build flags changed since."""
+    from paper_2508_07071_gb300.ncu_traffic import TRAFFIC, entry_hash
+    if not os.path.exists(TRAFFIC):
         return None
-    d = json.load(open(path)).get(key)
-    if not d or d.get("source_hash") != kernel_source_hash():
+    d = json.load(open(TRAFFIC)).get(key)
+    if not d or d.get("source_hash") != entry_hash(d):
         return None
     return int(d["dram_bytes_per_launch"])
 

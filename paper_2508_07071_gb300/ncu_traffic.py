@@ -3,12 +3,13 @@
 Reads the CSV that `ncu --metrics gpu__time_duration.sum,dram__bytes_read.sum,
 dram__bytes_write.sum --csv --log-file <f> <cmd>` writes, averages the
 launches whose kernel name matches a pattern, and records the result under a
-key in profiles/traffic.json together with the hash of the kernel sources and
-build flags it was measured on (bench.py reports the figure only while that
-hash still matches).
+key in profiles/traffic.json together with the list and hash of the sources
+the kernel is compiled from and of the build flags (bench.py reports the
+figure only while that hash still matches).
 
     python -m paper_2508_07071_gb300.ncu_traffic --csv launches.csv \\
-        --key nv12_letterbox_bf16_256 --kernel transform2d --command "<ncu command>"
+        --key nv12_letterbox_bf16_256 --kernel transform2d --unit k_nv12_bf16.cu \\
+        --command "<ncu command>"
 """
 from __future__ import annotations
 
@@ -24,20 +25,35 @@ ROOT = os.path.dirname(PKG)
 TRAFFIC = os.path.join(ROOT, "profiles", "traffic.json")
 
 
-def source_hash() -> str:
-    """Hash of every CUDA source and header of the library and of its build
-    script (flags change the kernels as much as sources do)."""
+def source_hash(files: list[str] | None = None) -> str:
+    """Hash of the CUDA sources a kernel is compiled from (paths relative to
+    csrc/; all of them when `files` is None) and of the build script (its
+    flags change the kernels as much as sources do)."""
     h = hashlib.sha256()
     base = os.path.join(PKG, "csrc")
-    for d, _, files in sorted(os.walk(base)):
-        for f in sorted(files):
-            if f.endswith((".cu", ".cuh", ".h")):
-                h.update(f.encode())
-                with open(os.path.join(d, f), "rb") as fh:
-                    h.update(fh.read())
+    if files is None:
+        files = sorted(os.path.relpath(os.path.join(d, f), base)
+                       for d, _, fs in os.walk(base) for f in fs if f.endswith((".cu", ".cuh", ".h")))
+    for rel in sorted(files):
+        h.update(rel.encode())
+        with open(os.path.join(base, rel), "rb") as fh:
+            h.update(fh.read())
     with open(os.path.join(PKG, "build.py"), "rb") as fh:
         h.update(fh.read())
     return h.hexdigest()[:16]
+
+
+# Every header the fused image-chain kernels are compiled with (registry.h
+# fixes the parameter-table capacity, a template argument of the kernels). A
+# traffic entry hashes these plus its translation unit; host-only sources
+# (api.cu, the other families) are not part of it.
+DEVICE_HEADERS = ["fkl/core.cuh", "fkl/ops.cuh", "fkl/dpp.cuh", "fkl/staged.cuh", "float_family.cuh",
+                  "registry.h"]
+
+
+def entry_hash(entry: dict) -> str:
+    """Hash over the sources an entry names (all sources for old entries)."""
+    return source_hash(entry.get("sources"))
 
 
 def parse_launches(path: str, kernel: str) -> list[dict]:
@@ -72,9 +88,11 @@ def main() -> None:
     ap.add_argument("--key", required=True)
     ap.add_argument("--kernel", default="transform2d", help="regular expression on the kernel name")
     ap.add_argument("--command", required=True, help="the ncu command line that wrote the CSV")
+    ap.add_argument("--unit", required=True, help="translation unit of the kernel, relative to csrc/")
     a = ap.parse_args()
     entry = summarise(parse_launches(a.csv, a.kernel))
-    entry["source_hash"] = source_hash()
+    entry["sources"] = sorted(DEVICE_HEADERS + [a.unit])
+    entry["source_hash"] = source_hash(entry["sources"])
     entry["command"] = a.command
     data = json.load(open(TRAFFIC)) if os.path.exists(TRAFFIC) else {}
     data[a.key] = entry

@@ -1,5 +1,6 @@
 """The ncu launch-list reader that records per-launch DRAM traffic."""
 import json
+import os
 
 from paper_2508_07071_gb300 import ncu_traffic as T
 
@@ -31,6 +32,9 @@ def test_parse_and_summarise(tmp_path):
 def test_source_hash_is_stable_and_short():
     a, b = T.source_hash(), T.source_hash()
     assert a == b and len(a) == 16 and int(a, 16) >= 0
+    part = T.source_hash(T.DEVICE_HEADERS + ["k_nv12_bf16.cu"])
+    assert part != a and part == T.entry_hash({"sources": T.DEVICE_HEADERS + ["k_nv12_bf16.cu"]})
+    assert T.entry_hash({}) == a  # an entry without a source list hashes everything
 
 
 def test_committed_traffic_file_is_well_formed():
@@ -39,3 +43,5 @@ def test_committed_traffic_file_is_well_formed():
         # the total and the parts are rounded separately
         assert abs(e["dram_bytes_per_launch"] - e["dram_read_bytes"] - e["dram_write_bytes"]) <= 2, key
         assert len(e["source_hash"]) == 16 and e["command"].startswith("ncu ")
+        for rel in e.get("sources", []):
+            assert os.path.exists(os.path.join(T.PKG, "csrc", rel)), rel
