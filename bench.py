@@ -519,7 +519,10 @@ def run_sweeps(args):
     Exp 4 (§VI-D) VF+HF: 50 images of 60x120 u8, 1..10,000 Mul+Add pairs;
     Exp 7 (§VI-G) data size: 100 .. 16,654,030 floats, 100 Mul+Add pairs;
     Exp 5 (§VI-E) instructions per op: 500 Mul/Add instructions on
-    3840*2160*8 floats split into N kernels of M = 500/N ops each."""
+    3840*2160*8 floats split into N kernels of M = 500/N ops each;
+    Exp 6 (§VI-F) host time of one call; Exp 9 (§VI-I) data types: 50
+    matrices of 60x120, Read -> Cast -> Mul -> Sub -> Div -> Write for every
+    (input, output) type pair. `--only exp4,exp9` runs a subset."""
     import torch
     import __graft_entry__
     __graft_entry__.build()
@@ -527,6 +530,10 @@ def run_sweeps(args):
 
     stream = torch.cuda.Stream()
     res = {"exp4_vf_hf": [], "exp7_data_size": [], "exp5_ops_per_kernel": []}
+    only = set(filter(None, args.only.split(",")))
+
+    def want(name):
+        return not only or name in only
 
     def t(fn, k):
         fn(stream)
@@ -536,9 +543,10 @@ def run_sweeps(args):
     with torch.cuda.stream(stream):
         # Exp 4: VF + HF, u8 input, batch 50 x 60 x 120 (one launch for the batch)
         n = 50 * 60 * 120
+        pairs_list = [1, 10, 100, 1000, 5000, 10000] if want("exp4") else []
         x = torch.from_numpy(synth.packed_image(40, 1, n, 1).reshape(-1)).cuda()
         y = torch.empty(n, device="cuda")
-        for pairs in [1, 10, 100, 1000, 5000, 10000]:
+        for pairs in pairs_list:
             kinds, consts = synth.chain_constants(40, 2 * pairs)
             p = F.Pipeline(W.vertical_chain(kinds, consts, u8_input=True))
             F.fkl_pipeline_autotune(p.handle, [F.as_fkl(x)], None, F.as_fkl(y), stream=stream, reps=5)
@@ -554,7 +562,7 @@ def run_sweeps(args):
         # Exp 7: data size, 100 Mul+Add pairs, float32
         kinds, consts = synth.chain_constants(41, 200)
         p = F.Pipeline(W.vertical_chain(kinds, consts))
-        for n in [100, 10_000, 282_370, 1_000_000, 9_032_740, 16_654_030]:
+        for n in [100, 10_000, 282_370, 1_000_000, 9_032_740, 16_654_030] if want("exp7") else []:
             x = torch.from_numpy(synth.f32_uniform(41, n)).cuda()
             y = torch.empty_like(x)
             F.fkl_pipeline_autotune(p.handle, [F.as_fkl(x)], None, F.as_fkl(y), stream=stream, reps=5)
@@ -566,60 +574,105 @@ def run_sweeps(args):
                                           "fused_GBps": round(8 * n / fused / 1e6, 1)})
             print(json.dumps({"exp7": res["exp7_data_size"][-1]}), flush=True)
         # Exp 5: 500 instructions split into N kernels of M ops (M * N = 500)
-        n = 3840 * 2160 * 8
-        x = torch.from_numpy(synth.f32_uniform(42, n)).cuda()
-        y = torch.empty_like(x)
-        kinds, consts = synth.chain_constants(42, 500)
-        full = F.Pipeline(W.vertical_chain(kinds, consts))
-        F.fkl_pipeline_autotune(full.handle, [F.as_fkl(x)], None, F.as_fkl(y), stream=stream, reps=3)
-        fused = t(lambda st: F.fkl_execute(full.handle, F.as_fkl(x), F.as_fkl(y), stream=st), 5)
-        for m in [1, 5, 25, 100, 250, 500]:
-            parts = [F.Pipeline(W.vertical_chain(kinds[i:i + m], consts[i:i + m])) for i in range(0, 500, m)]
-            for q in parts:
-                F.fkl_pipeline_set_shape(q.handle, F.fkl_pipeline_get_shape(full.handle))
+        if want("exp5"):
+            n = 3840 * 2160 * 8
+            x = torch.from_numpy(synth.f32_uniform(42, n)).cuda()
+            y = torch.empty_like(x)
+            kinds, consts = synth.chain_constants(42, 500)
+            full = F.Pipeline(W.vertical_chain(kinds, consts))
+            F.fkl_pipeline_autotune(full.handle, [F.as_fkl(x)], None, F.as_fkl(y), stream=stream, reps=3)
+            fused = t(lambda st: F.fkl_execute(full.handle, F.as_fkl(x), F.as_fkl(y), stream=st), 5)
+            for m in [1, 5, 25, 100, 250, 500]:
+                parts = [F.Pipeline(W.vertical_chain(kinds[i:i + m], consts[i:i + m])) for i in range(0, 500, m)]
+                for q in parts:
+                    F.fkl_pipeline_set_shape(q.handle, F.fkl_pipeline_get_shape(full.handle))
 
-            def chain(st):
-                F.fkl_execute(parts[0].handle, F.as_fkl(x), F.as_fkl(y), stream=st)
-                for q in parts[1:]:
-                    F.fkl_execute(q.handle, F.as_fkl(y), F.as_fkl(y), stream=st)
-            split = t(chain, 3)
-            res["exp5_ops_per_kernel"].append({"ops_per_kernel": m, "kernels": len(parts),
-                                               "split_ms": round(split, 3), "fused_500_ms": round(fused, 3),
-                                               "speedup": round(split / fused, 2)})
-            print(json.dumps({"exp5": res["exp5_ops_per_kernel"][-1]}), flush=True)
+                def chain(st):
+                    F.fkl_execute(parts[0].handle, F.as_fkl(x), F.as_fkl(y), stream=st)
+                    for q in parts[1:]:
+                        F.fkl_execute(q.handle, F.as_fkl(y), F.as_fkl(y), stream=st)
+                split = t(chain, 3)
+                res["exp5_ops_per_kernel"].append({"ops_per_kernel": m, "kernels": len(parts),
+                                                   "split_ms": round(split, 3), "fused_500_ms": round(fused, 3),
+                                                   "speedup": round(split / fused, 2)})
+                print(json.dumps({"exp5": res["exp5_ops_per_kernel"][-1]}), flush=True)
         # Exp 6: host time of one call, fused vs one launch per op and image:
-        # Batch(Crop -> Resize 64x128 -> BGR->RGB -> Mul -> Sub -> Div -> Split)
-        import ctypes
-        frame = torch.from_numpy(synth.packed_image(43, 2160, 3840)).cuda()
-        p = F.Pipeline(W.normalize_chain(64, 128))
-        res["exp6_cpu_time"] = []
-        for n in [2, 10, 50, 100, 152]:
-            rois = np.ascontiguousarray(synth.crop_rois(43, n, 3840, 2160, (32, 640), (32, 480)))
-            out = torch.empty((n, 3, 128, 64), device="cuda")
-            arr = (F.fkl_tensor * n)(*([F.as_fkl(frame)] * n))
-            rp = rois.ctypes.data_as(ctypes.POINTER(ctypes.c_int32))
-            o = F.as_fkl(out, F.FKL_LAYOUT_NCHW)
-            nb = F.fkl_unfused_workspace_bytes(p.handle, list(arr), rois, o)
-            ws = torch.empty(nb, dtype=torch.uint8, device="cuda")
-            sh = stream.cuda_stream
+        if want("exp6"):
+            # Batch(Crop -> Resize 64x128 -> BGR->RGB -> Mul -> Sub -> Div -> Split)
+            import ctypes
+            frame = torch.from_numpy(synth.packed_image(43, 2160, 3840)).cuda()
+            p = F.Pipeline(W.normalize_chain(64, 128))
+            res["exp6_cpu_time"] = []
+            for n in [2, 10, 50, 100, 152]:
+                rois = np.ascontiguousarray(synth.crop_rois(43, n, 3840, 2160, (32, 640), (32, 480)))
+                out = torch.empty((n, 3, 128, 64), device="cuda")
+                arr = (F.fkl_tensor * n)(*([F.as_fkl(frame)] * n))
+                rp = rois.ctypes.data_as(ctypes.POINTER(ctypes.c_int32))
+                o = F.as_fkl(out, F.FKL_LAYOUT_NCHW)
+                nb = F.fkl_unfused_workspace_bytes(p.handle, list(arr), rois, o)
+                ws = torch.empty(nb, dtype=torch.uint8, device="cuda")
+                sh = stream.cuda_stream
 
-            def host_us(call, reps):
-                call()
-                torch.cuda.synchronize()
-                t0 = time.perf_counter()
-                for _ in range(reps):
+                def host_us(call, reps):
                     call()
-                dt = (time.perf_counter() - t0) / reps
-                torch.cuda.synchronize()
-                return dt * 1e6
-            fused = host_us(lambda: F._lib.fkl_execute_batch(p.handle, n, arr, rp, ctypes.byref(o), sh), 200)
-            unf = host_us(lambda: F._lib.fkl_execute_batch_unfused(p.handle, n, arr, rp, ctypes.byref(o),
-                                                                   ws.data_ptr(), nb, sh), 20)
-            res["exp6_cpu_time"].append({"batch": n, "fused_host_us": round(fused, 2),
-                                         "unfused_host_us": round(unf, 1), "launches_unfused": 6 * n,
-                                         "speedup": round(unf / fused, 1)})
-            print(json.dumps({"exp6": res["exp6_cpu_time"][-1]}), flush=True)
-    print(json.dumps({"metric": "paper sweeps (Exp 4, 5, 6, 7) on GB300", "results": res}), flush=True)
+                    torch.cuda.synchronize()
+                    t0 = time.perf_counter()
+                    for _ in range(reps):
+                        call()
+                    dt = (time.perf_counter() - t0) / reps
+                    torch.cuda.synchronize()
+                    return dt * 1e6
+                fused = host_us(lambda: F._lib.fkl_execute_batch(p.handle, n, arr, rp, ctypes.byref(o), sh), 200)
+                unf = host_us(lambda: F._lib.fkl_execute_batch_unfused(p.handle, n, arr, rp, ctypes.byref(o),
+                                                                       ws.data_ptr(), nb, sh), 20)
+                res["exp6_cpu_time"].append({"batch": n, "fused_host_us": round(fused, 2),
+                                             "unfused_host_us": round(unf, 1), "launches_unfused": 6 * n,
+                                             "speedup": round(unf / fused, 1)})
+                print(json.dumps({"exp6": res["exp6_cpu_time"][-1]}), flush=True)
+        # Exp 9: data types, 50 x 60x120, Read -> Cast -> Mul -> Sub -> Div -> Write.
+        # "eager": one call per step from pre-marshalled arguments (what the
+        # host submits is part of the time, as in the paper's measurement);
+        # "graph": the same calls captured once in a CUDA graph and replayed
+        # (device time only).
+        import ctypes
+        cfg = W.DTYPES
+        res["exp9_data_types"] = []
+        L = cfg["rows"] * cfg["cols"]
+        code = {"u8": F.FKL_U8, "u16": F.FKL_U16, "f32": F.FKL_F32, "f64": F.FKL_F64}
+        size = {"u8": 1, "u16": 2, "f32": 4, "f64": 8}
+        nt = cfg["n"]
+        for src in cfg["ins"] if want("exp9") else []:
+            xs = [torch.from_numpy(synth.linear_values(100 + i, L, src)).cuda() for i in range(nt)]
+            arr = (F.fkl_tensor * nt)(*[F.as_fkl(x) for x in xs])
+            for dst in cfg["outs"]:
+                y = torch.empty(nt * L, dtype=torch.float32 if dst == "f32" else torch.float64, device="cuda")
+                o = F.as_fkl(y)
+                p = F.Pipeline(W.typed_chain(code[src], code[dst], cfg["mul"], cfg["sub"], cfg["div"]))
+                F.fkl_pipeline_autotune(p.handle, list(arr), None, o, stream=stream, reps=7)
+                h = p.handle
+
+                def fused_call(st):
+                    F._check(F._lib.fkl_execute_batch(h, nt, arr, None, ctypes.byref(o), st.cuda_stream))
+
+                def unfused_call(st):
+                    F._check(F._lib.fkl_execute_batch_unfused(h, nt, arr, None, ctypes.byref(o), None, 0,
+                                                              st.cuda_stream))
+                row = {"in": src, "out": dst}
+                for name, call, k in (("fused", fused_call, 50), ("unfused", unfused_call, 10)):
+                    row[name + "_eager_us"] = round(1000 * t(call, k), 2)
+                    g = torch.cuda.CUDAGraph()
+                    with torch.cuda.graph(g, stream=stream):
+                        call(stream)
+                    g.replay()
+                    row[name + "_graph_us"] = round(1000 * t(lambda st: g.replay(), k), 2)
+                row["speedup_eager"] = round(row["unfused_eager_us"] / row["fused_eager_us"], 1)
+                row["speedup_graph"] = round(row["unfused_graph_us"] / row["fused_graph_us"], 1)
+                row["launches_unfused"] = 4 * nt
+                row["fused_graph_GBps"] = round(nt * L * (size[src] + size[dst]) / row["fused_graph_us"] / 1e3, 1)
+                row["shape"] = list(F.fkl_pipeline_get_shape(h))
+                res["exp9_data_types"].append(row)
+                print(json.dumps({"exp9": row}), flush=True)
+    print(json.dumps({"metric": "paper sweeps (Exp 4, 5, 6, 7, 9) on GB300", "results": res}), flush=True)
 
 
 def run_reference(args):
@@ -685,6 +738,7 @@ def main():
     ap.add_argument("--no-autotune", action="store_true")
     ap.add_argument("--autotune-reps", type=int, default=7)
     ap.add_argument("--shape", default="", help="vec,tx,ty,ry launch shape (skips the autotuner)")
+    ap.add_argument("--only", default="", help="sweeps: comma-separated subset of exp4,exp5,exp6,exp7,exp9")
     args = ap.parse_args()
     if args.warmup < 3:
         raise SystemExit("--warmup must be >= 3")

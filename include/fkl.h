@@ -59,7 +59,9 @@ enum {                 /* element types                                     */
   FKL_F32 = 1,
   FKL_F16 = 2,         /* IEEE binary16                                     */
   FKL_BF16 = 3,
-  FKL_E4M3 = 4         /* OCP FP8 E4M3 (finite-only, max 448)               */
+  FKL_E4M3 = 4,        /* OCP FP8 E4M3 (finite-only, max 448)               */
+  FKL_U16 = 5,         /* typed chains (inputs)                             */
+  FKL_F64 = 6          /* typed chains (inputs and outputs)                 */
 };
 
 enum {                 /* layouts and the meaning of dims[]                 */
@@ -91,7 +93,9 @@ enum {
   FKL_OP_READ_NV12 = 2,  /* NV12 frame, decoded BT.601 limited range to RGB */
   FKL_OP_READ_F32 = 3,   /* linear float32 tensor                           */
   FKL_OP_READ_U8 = 4,    /* linear u8 tensor, converted to float exactly
-                            (vertical chains)                              */
+                            (vertical and typed chains)                    */
+  FKL_OP_READ_U16 = 5,   /* linear u16 tensor (typed chains)                */
+  FKL_OP_READ_F64 = 6,   /* linear float64 tensor (typed chains)            */
 
   /* Read modifiers: together with the source they form the one ROp.       */
   FKL_OP_CROP = 10,      /* i[0..3] = x, y, w, h of the window read        */
@@ -143,6 +147,12 @@ typedef struct fkl_pipeline_s* fkl_pipeline;  /* library-owned handle        */
  *   READ_NV12 (RESIZE|LETTERBOX) [SWAP_RB] [MUL] [ADD|SUB] [DIV] WRITE_{SPLIT,PACKED}
  *   READ_U8C3 [CROP] [SWAP_RB] [ADD_SAT_U8] WRITE_{SPLIT,PACKED} (U8 output)
  *   READ_F32|READ_U8 (MUL|ADD){0..65536} WRITE_PACKED(F32)   (vertical chain)
+ *   READ_U8|READ_U16|READ_F32|READ_F64 [MUL] [ADD|SUB] [DIV] WRITE_PACKED(F32|F64)
+ *        (typed chain, paper §VI-I Read -> Cast -> Multiply -> Subtract ->
+ *        Divide -> Write: the input is cast to the output type, then every
+ *        op runs and rounds once in the output type, constants f[0] taken
+ *        exactly into it; a READ_F32|READ_U8 chain of MUL/ADD only writing
+ *        F32 is a vertical chain)
  * An absent MUL/ADD/SUB/DIV is bound as its identity (x*1, x-0, x/1 are
  * exact, so the result equals the shorter chain bit for bit). A chain of the
  * right grammar outside this set returns FKL_ERR_UNSUPPORTED.
@@ -159,7 +169,9 @@ FKL_API fkl_status fkl_pipeline_create(const fkl_op_desc* ops, int32_t n_ops,
  * NHWC (WRITE_PACKED) with N = 1 and the dtype the WOp names; its H, W must
  * equal the RESIZE/LETTERBOX size (the ROI size when there is no resize).
  * Vertical chains: `in` (LINEAR F32, or U8 for READ_U8) and `out` (LINEAR
- * F32) have the same length (F32 input may alias the output). stream is a cudaStream_t. One kernel launch per call (vertical
+ * F32) have the same length (F32 input may alias the output). Typed chains:
+ * `in` LINEAR of the read's type, `out` LINEAR of the write's type, same
+ * length (a batch of one). stream is a cudaStream_t. One kernel launch per call (vertical
  * chains longer than 4096 ops use one launch per 4096 ops).
  */
 FKL_API fkl_status fkl_execute(fkl_pipeline p, const fkl_tensor* in, fkl_tensor* out,
@@ -173,6 +185,11 @@ FKL_API fkl_status fkl_execute(fkl_pipeline p, const fkl_tensor* in, fkl_tensor*
  * descriptor (or the whole image) for every image. Every ROI must lie inside
  * its image. One launch covers up to 256 images; larger n uses ceil(n/256)
  * launches.
+ * Tensor chains (vertical and typed): n LINEAR tensors of the read's type and
+ * one common length L (each its own pointer) into one LINEAR output of n * L
+ * elements of the write's type, tensor i at elements [i * L, (i + 1) * L);
+ * rois must be NULL; an empty batch may pass NULL data. Typed chains run in
+ * one launch per 256 tensors, vertical chains in one launch per tensor.
  */
 FKL_API fkl_status fkl_execute_batch(fkl_pipeline p, int32_t n, const fkl_tensor* ins,
                              const int32_t* rois, fkl_tensor* out,
@@ -199,8 +216,10 @@ FKL_API const char* fkl_last_error(void);
  * fkl_execute_batch_unfused needs for these arguments. This is also the
  * device memory that fusion saves (paper §VI-L).
  * fkl_execute_batch_unfused: `workspace` is caller-owned device memory of at
- * least that size, 256-byte aligned. Launch count = n * (ops in the chain),
- * except vertical chains (one launch per Mul/Add over the whole tensor).
+ * least that size, 256-byte aligned. Launch count = n * (ops in the chain).
+ * Tensor chains (vertical and typed) need no workspace (0 bytes; each op
+ * runs in place on the output): one kernel per tensor and op (for typed
+ * chains the first kernel reads, casts and writes the output).
  */
 FKL_API fkl_status fkl_unfused_workspace_bytes(fkl_pipeline p, int32_t n,
                                        const fkl_tensor* ins,

@@ -31,7 +31,10 @@ here are:
   * saturating u8 arithmetic clamps the exact integer result; float -> u8
     rounds half to even then clamps;
   * the vertical Mul/Add chain (§VI-B) is evaluated in float32 in chain order,
-    every op rounded on its own (no multiply-add contraction).
+    every op rounded on its own (no multiply-add contraction);
+  * the typed chains of the data-type experiment (§VI-I: Read -> Cast ->
+    Multiply -> Subtract -> Divide -> Write) cast the input to the output
+    type and run every op in that type, each rounded on its own.
 
 Functions that no test pins against something other than themselves say
 "parity unpinned" in their docstring; at present there are none.
@@ -299,6 +302,31 @@ def vertical_chain_f32(x: np.ndarray, kinds, consts) -> np.ndarray:
             y = np.add(y, c32, dtype=np.float32)
         else:
             raise ValueError(f"unknown op kind {kind}")
+    return y
+
+
+_TYPES = {"u8": np.uint8, "u16": np.uint16, "f32": np.float32, "f64": np.float64}
+
+
+def typed_chain(x: np.ndarray, out_dtype: str, mul=None, sub=None, div=None) -> np.ndarray:
+    """Read -> Cast -> Multiply -> Subtract -> Divide -> Write (§VI-I).
+
+    The input is cast to the output type (numpy's cast: exact for u8, u16 and
+    f32 into f32 or f64; round to nearest even for f64 into f32); then each
+    present op is one numpy operation in that type, rounded to it before the
+    next op reads it. The constants are float32 values (what a descriptor
+    carries) taken exactly into the output type. An absent op is skipped.
+    """
+    ct = _TYPES[out_dtype]
+    if ct not in (np.float32, np.float64):
+        raise ValueError("typed chains write f32 or f64")
+    y = np.asarray(x).astype(ct)
+    if mul is not None:
+        y = np.multiply(y, ct(np.float32(mul)), dtype=ct)
+    if sub is not None:
+        y = np.subtract(y, ct(np.float32(sub)), dtype=ct)
+    if div is not None:
+        y = np.divide(y, ct(np.float32(div)), dtype=ct)
     return y
 
 

@@ -44,6 +44,10 @@ int dtype_bytes(int dt) {
       return 2;
     case FKL_F32:
       return 4;
+    case FKL_U16:
+      return 2;
+    case FKL_F64:
+      return 8;
     default:
       return 0;
   }
@@ -61,19 +65,59 @@ const char* dtype_name(int dt) {
       return "bf16";
     case FKL_E4M3:
       return "e4m3";
+    case FKL_U16:
+      return "u16";
+    case FKL_F64:
+      return "f64";
     default:
       return "?";
   }
 }
 
-bool is_read(int op) {
-  return op == FKL_OP_READ_U8C3 || op == FKL_OP_READ_NV12 || op == FKL_OP_READ_F32 || op == FKL_OP_READ_U8;
+bool is_linear_read(int op) {
+  return op == FKL_OP_READ_F32 || op == FKL_OP_READ_U8 || op == FKL_OP_READ_U16 || op == FKL_OP_READ_F64;
 }
+bool is_read(int op) { return op == FKL_OP_READ_U8C3 || op == FKL_OP_READ_NV12 || is_linear_read(op); }
 bool is_write(int op) { return op == FKL_OP_WRITE_PACKED || op == FKL_OP_WRITE_SPLIT; }
 bool is_modifier(int op) { return op == FKL_OP_CROP || op == FKL_OP_RESIZE || op == FKL_OP_LETTERBOX; }
 bool is_compute(int op) {
   return op == FKL_OP_SWAP_RB || op == FKL_OP_MUL || op == FKL_OP_ADD || op == FKL_OP_SUB ||
          op == FKL_OP_DIV || op == FKL_OP_ADD_SAT_U8;
+}
+
+// Typed chains: READ_{U8,U16,F32,F64} [MUL] [ADD|SUB] [DIV] WRITE_PACKED(F32|F64).
+fkl_status parse_typed(const fkl_op_desc* ops, int n, int src, Spec& s) {
+  s.family = FAM_CAST;
+  s.in_dtype = src == FKL_OP_READ_U8 ? FKL_U8 : src == FKL_OP_READ_U16 ? FKL_U16
+               : src == FKL_OP_READ_F32 ? FKL_F32 : FKL_F64;
+  if (ops[n - 1].op != FKL_OP_WRITE_PACKED || (s.out_dtype != FKL_F32 && s.out_dtype != FKL_F64))
+    return fail(FKL_ERR_UNSUPPORTED, "typed tensor chains write packed F32 or F64");
+  int stage = 0;  // compiled order: MUL, ADD|SUB, DIV
+  for (int k = 1; k < n - 1; ++k) {
+    const fkl_op_desc& d = ops[k];
+    int want;
+    if (d.op == FKL_OP_MUL) {
+      want = 1;
+      s.has_mul = true;
+      s.mul[0] = d.f[0];
+    } else if (d.op == FKL_OP_ADD || d.op == FKL_OP_SUB) {
+      want = 2;
+      s.has_sub = true;
+      s.sub[0] = d.op == FKL_OP_SUB ? d.f[0] : -d.f[0];  // x + c == x - (-c), bit for bit
+    } else if (d.op == FKL_OP_DIV) {
+      want = 3;
+      s.has_div = true;
+      s.div[0] = d.f[0];
+    } else if (is_modifier(d.op)) {
+      return fail(FKL_ERR_INVALID, "op %d: read modifiers apply to image reads only", k);
+    } else {
+      return fail(FKL_ERR_UNSUPPORTED, "op %d: typed tensor chains take [MUL] [ADD|SUB] [DIV]", k);
+    }
+    if (want <= stage)
+      return fail(FKL_ERR_UNSUPPORTED, "op %d: typed tensor chains take MUL, then ADD|SUB, then DIV", k);
+    stage = want;
+  }
+  return FKL_OK;
 }
 
 // ROp -> COp* -> WOp grammar, then the compiled-family table.
@@ -100,7 +144,15 @@ fkl_status parse(const fkl_op_desc* ops, int n, Spec& s) {
     s.fp8_scale = sc;
   }
 
-  if (src == FKL_OP_READ_F32 || src == FKL_OP_READ_U8) {
+  if (is_linear_read(src)) {
+    bool mul_add_only = true;
+    for (int k = 1; k < n - 1; ++k) {
+      if (is_modifier(ops[k].op)) return fail(FKL_ERR_INVALID, "op %d: read modifiers apply to image reads only", k);
+      mul_add_only = mul_add_only && (ops[k].op == FKL_OP_MUL || ops[k].op == FKL_OP_ADD);
+    }
+    const bool vertical = (src == FKL_OP_READ_F32 || src == FKL_OP_READ_U8) && mul_add_only &&
+                          wop == FKL_OP_WRITE_PACKED && odt == FKL_F32;
+    if (!vertical) return parse_typed(ops, n, src, s);
     s.family = FAM_VCHAIN;
     s.vinput_u8 = src == FKL_OP_READ_U8;
     for (int k = 1; k < n - 1; ++k) {
@@ -184,6 +236,8 @@ fkl_status parse(const fkl_op_desc* ops, int n, Spec& s) {
     return FKL_OK;
   }
   s.family = src == FKL_OP_READ_U8C3 ? FAM_PACKED : FAM_NV12;
+  if (odt == FKL_U16 || odt == FKL_F64)
+    return fail(FKL_ERR_UNSUPPORTED, "image chains write U8, F32, F16, BF16 or E4M3");
   if (!s.split && odt != FKL_F32) return fail(FKL_ERR_UNSUPPORTED, "packed float outputs are F32 only");
   return FKL_OK;
 }
@@ -396,6 +450,12 @@ cudaError_t device_error_flag(int** out) {
 
 std::vector<fkl_launch_shape> shapes_for(const Spec& s) {
   std::vector<int> vecs;
+  if (s.family == FAM_CAST) {  // {elements per thread, threads, 1, 1}
+    std::vector<fkl_launch_shape> out;
+    for (int v : {8, 16})
+      for (int tx : {128, 256}) out.push_back(fkl_launch_shape{v, tx, 1, 1});
+    return out;
+  }
   if (s.family == FAM_INT) {
     vecs = {16};
   } else if (s.family == FAM_PACKED || s.family == FAM_NV12) {
@@ -427,6 +487,7 @@ std::vector<fkl_launch_shape> shapes_for(const Spec& s) {
 fkl_launch_shape default_shape(const Spec& s) {
   if (s.family == FAM_INT) return {16, 16, 8, 1};
   if (s.family == FAM_VCHAIN) return {16, 256, 1, 1};
+  if (s.family == FAM_CAST) return {8, 256, 1, 1};
   return {s.out_dtype == FKL_F32 ? 4 : 8, 16, 8, 1};
 }
 
@@ -451,6 +512,12 @@ std::string make_name(const Spec& s) {
     case FAM_VCHAIN:
       n += "ReadF32";
       break;
+    case FAM_CAST:
+      n = std::string("fused:Read<") + dtype_name(s.in_dtype) + ">>Cast<" + dtype_name(s.out_dtype) + ">";
+      if (s.has_mul) n += ">Mul";
+      if (s.has_sub) n += ">Sub";
+      if (s.has_div) n += ">Div";
+      return n + ">Write<" + dtype_name(s.out_dtype) + ">";
   }
   if (s.family == FAM_VCHAIN) {
     if (s.vinput_u8) n = "fused:ReadU8";
@@ -487,24 +554,72 @@ cudaError_t launch_family(const LaunchCtx& c) {
   }
 }
 
-fkl_status check_linear(const Spec& s, const fkl_tensor* in, const fkl_tensor* out, int64_t& n) {
-  if (!in || !out || !in->data || !out->data) return fail(FKL_ERR_INVALID, "tensor missing");
-  const int in_dt = s.vinput_u8 ? FKL_U8 : FKL_F32;
-  if (in->layout != FKL_LAYOUT_LINEAR || out->layout != FKL_LAYOUT_LINEAR || in->dtype != in_dt ||
-      out->dtype != FKL_F32)
-    return fail(FKL_ERR_INVALID, "tensor chains need a LINEAR %s input and a LINEAR F32 output",
-                s.vinput_u8 ? "U8" : "F32");
-  if (in->dims[0] != out->dims[0] || in->dims[0] < 0)
-    return fail(FKL_ERR_INVALID, "input and output lengths differ (%lld vs %lld)", (long long)in->dims[0],
-                (long long)out->dims[0]);
-  n = in->dims[0];
+// Tensor chains (vertical and typed): n LINEAR inputs of the read's type and
+// one length, one LINEAR output of n * length elements of the write's type
+// (tensor i at elements [i * length, (i + 1) * length)).
+fkl_status check_linear(const Spec& s, int32_t n, const fkl_tensor* ins, const int32_t* rois,
+                        const fkl_tensor* out, int64_t& len, std::vector<const void*>& ptrs) {
+  const int in_dt = s.family == FAM_CAST ? s.in_dtype : (s.vinput_u8 ? FKL_U8 : FKL_F32);
+  const int out_dt = s.family == FAM_CAST ? s.out_dtype : FKL_F32;
+  if (n < 0) return fail(FKL_ERR_INVALID, "negative batch size");
+  if (rois) return fail(FKL_ERR_INVALID, "tensor chains take no ROIs");
+  if (n > 0 && !ins) return fail(FKL_ERR_INVALID, "inputs missing");
+  if (!out) return fail(FKL_ERR_INVALID, "output tensor missing");
+  if (out->layout != FKL_LAYOUT_LINEAR || out->dtype != out_dt)
+    return fail(FKL_ERR_INVALID, "tensor chains need a LINEAR %s output", dtype_name(out_dt));
+  len = n > 0 ? ins[0].dims[0] : 0;
+  try {
+    ptrs.resize(n);
+  } catch (...) {
+    return fail(FKL_ERR_OOM, "host allocation failed");
+  }
+  for (int i = 0; i < n; ++i) {
+    const fkl_tensor& t = ins[i];
+    if (t.layout != FKL_LAYOUT_LINEAR || t.dtype != in_dt)
+      return fail(FKL_ERR_INVALID, "input %d must be LINEAR %s", i, dtype_name(in_dt));
+    if (t.dims[0] != len || len < 0)
+      return fail(FKL_ERR_INVALID, "input %d has %lld elements, input 0 has %lld", i, (long long)t.dims[0],
+                  (long long)len);
+    if (!t.data && len > 0) return fail(FKL_ERR_INVALID, "input %d: data is NULL", i);
+    ptrs[i] = t.data;
+  }
+  if (len > (int64_t(1) << 40) || out->dims[0] != int64_t(n) * len)
+    return fail(FKL_ERR_INVALID, "output must hold n x length = %lld elements (has %lld)",
+                (long long)(int64_t(n) * len), (long long)out->dims[0]);
+  if (!out->data && n * len > 0) return fail(FKL_ERR_INVALID, "output tensor missing");
   return FKL_OK;
 }
+
+// Runs a tensor chain: typed chains in one launch per 256 tensors, vertical
+// chains one launch per tensor (and per 4096 ops); unfused: one kernel per op.
+fkl_status run_linear(fkl_pipeline p, int32_t n, const fkl_tensor* ins, const int32_t* rois, fkl_tensor* out,
+                      bool unfused, void* stream) {
+  int64_t len = 0;
+  std::vector<const void*> ptrs;
+  const fkl_status st = check_linear(p->spec, n, ins, rois, out, len, ptrs);
+  if (st != FKL_OK) return st;
+  if (n == 0 || len == 0) return FKL_OK;
+  const cudaStream_t cs = static_cast<cudaStream_t>(stream);
+  cudaError_t e = cudaSuccess;
+  if (p->spec.family == FAM_CAST) {
+    e = unfused ? launch_unfused_cast(p->spec, n, ptrs.data(), out->data, len, cs)
+                : launch_cast(p->spec, p->shape, n, ptrs.data(), out->data, len, cs);
+  } else {
+    for (int i = 0; i < n && e == cudaSuccess; ++i) {
+      float* o = static_cast<float*>(out->data) + i * len;
+      e = unfused ? launch_unfused_vchain(p->spec, ptrs[i], o, len, cs)
+                  : launch_vchain(p->spec, p->shape, ptrs[i], o, len, cs);
+    }
+  }
+  return e == cudaSuccess ? FKL_OK : cuda_fail(e, unfused ? "unfused launch" : "tensor chain launch");
+}
+
+bool is_tensor_chain(const Spec& s) { return s.family == FAM_VCHAIN || s.family == FAM_CAST; }
 
 fkl_status validate_batch(const fkl_pipeline p, int32_t n, const fkl_tensor* ins, const int32_t* rois,
                           const fkl_tensor* out, OutDesc& od, std::vector<fkl::ResampleParams>& imgs) {
   if (!p) return fail(FKL_ERR_INVALID, "null pipeline");
-  if (p->spec.family == FAM_VCHAIN) return fail(FKL_ERR_INVALID, "float32 tensor chains run through fkl_execute");
+  if (is_tensor_chain(p->spec)) return fail(FKL_ERR_INVALID, "tensor chains take LINEAR tensors");
   if (n < 0) return fail(FKL_ERR_INVALID, "negative batch size");
   if (n > 0 && !ins) return fail(FKL_ERR_INVALID, "inputs missing");
   fkl_status st = check_out(p->spec, out, n, od);
@@ -528,6 +643,7 @@ namespace {
 // fkl_execute_batch with an optional device-side FP8 scale.
 fkl_status execute_batch_impl(fkl_pipeline p, int32_t n, const fkl_tensor* ins, const int32_t* rois,
                               fkl_tensor* out, const float* scale_inv_dev, void* stream) {
+  if (p && is_tensor_chain(p->spec)) return run_linear(p, n, ins, rois, out, false, stream);
   OutDesc od;
   std::vector<fkl::ResampleParams> imgs;
   fkl_status st = validate_batch(p, n, ins, rois, out, od, imgs);
@@ -658,15 +774,6 @@ fkl_status fkl_reduce_batch(fkl_pipeline p, int32_t n, const fkl_tensor* ins, co
 
 fkl_status fkl_execute(fkl_pipeline p, const fkl_tensor* in, fkl_tensor* out, void* stream) {
   if (!p) return fail(FKL_ERR_INVALID, "null pipeline");
-  if (p->spec.family == FAM_VCHAIN) {
-    int64_t n = 0;
-    const fkl_status st = check_linear(p->spec, in, out, n);
-    if (st != FKL_OK) return st;
-    if (n == 0) return FKL_OK;
-    const cudaError_t e = launch_vchain(p->spec, p->shape, in->data, static_cast<float*>(out->data), n,
-                                        static_cast<cudaStream_t>(stream));
-    return e == cudaSuccess ? FKL_OK : cuda_fail(e, "vertical chain launch");
-  }
   return fkl_execute_batch(p, 1, in, nullptr, out, stream);
 }
 
@@ -675,7 +782,7 @@ fkl_status fkl_unfused_workspace_bytes(fkl_pipeline p, int32_t n, const fkl_tens
   if (!bytes) return fail(FKL_ERR_INVALID, "bytes is NULL");
   *bytes = 0;
   if (!p) return fail(FKL_ERR_INVALID, "null pipeline");
-  if (p->spec.family == FAM_VCHAIN) return FKL_OK;
+  if (p->spec.family == FAM_VCHAIN || p->spec.family == FAM_CAST) return FKL_OK;  // in place on `out`
   OutDesc od;
   std::vector<fkl::ResampleParams> imgs;
   const fkl_status st = validate_batch(p, n, ins, rois, out, od, imgs);
@@ -693,15 +800,7 @@ fkl_status fkl_execute_batch_unfused(fkl_pipeline p, int32_t n, const fkl_tensor
                                      fkl_tensor* out, void* workspace, size_t workspace_bytes, void* stream) {
   if (!p) return fail(FKL_ERR_INVALID, "null pipeline");
   const cudaStream_t s = static_cast<cudaStream_t>(stream);
-  if (p->spec.family == FAM_VCHAIN) {
-    if (n != 1) return fail(FKL_ERR_INVALID, "float32 tensor chains take one tensor (n = 1)");
-    int64_t len = 0;
-    const fkl_status st = check_linear(p->spec, ins, out, len);
-    if (st != FKL_OK) return st;
-    if (len == 0) return FKL_OK;
-    const cudaError_t e = launch_unfused_vchain(p->spec, ins->data, static_cast<float*>(out->data), len, s);
-    return e == cudaSuccess ? FKL_OK : cuda_fail(e, "unfused launch");
-  }
+  if (is_tensor_chain(p->spec)) return run_linear(p, n, ins, rois, out, true, stream);  // in place: no scratch
   size_t need = 0;
   fkl_status st = fkl_unfused_workspace_bytes(p, n, ins, rois, out, &need);
   if (st != FKL_OK) return st;
@@ -818,15 +917,7 @@ fkl_status fkl_execute_batch_unfused_static(fkl_pipeline p, int32_t n, const fkl
                                             fkl_tensor* out, void* stream) {
   if (!p) return fail(FKL_ERR_INVALID, "null pipeline");
   const cudaStream_t s = static_cast<cudaStream_t>(stream);
-  if (p->spec.family == FAM_VCHAIN) {  // one kernel per op, in place on `out`: no scratch
-    if (n != 1) return fail(FKL_ERR_INVALID, "float32 tensor chains take one tensor (n = 1)");
-    int64_t len = 0;
-    const fkl_status st = check_linear(p->spec, ins, out, len);
-    if (st != FKL_OK) return st;
-    if (len == 0) return FKL_OK;
-    const cudaError_t e = launch_unfused_vchain(p->spec, ins->data, static_cast<float*>(out->data), len, s);
-    return e == cudaSuccess ? FKL_OK : cuda_fail(e, "unfused launch");
-  }
+  if (is_tensor_chain(p->spec)) return run_linear(p, n, ins, rois, out, true, stream);  // in place: no scratch
   if (n < 0) return fail(FKL_ERR_INVALID, "negative batch size");
   if (n > 0 && !ins) return fail(FKL_ERR_INVALID, "inputs missing");
   OutDesc od;

@@ -11,7 +11,7 @@
 
 namespace fkl_impl {
 
-enum Family { FAM_PACKED = 1, FAM_NV12 = 2, FAM_INT = 3, FAM_VCHAIN = 4 };
+enum Family { FAM_PACKED = 1, FAM_NV12 = 2, FAM_INT = 3, FAM_VCHAIN = 4, FAM_CAST = 5 };
 enum Geom { GEOM_NONE = 0, GEOM_RESIZE = 1, GEOM_LETTERBOX = 2 };
 
 // A parsed chain: which compiled family runs it and the runtime parameters
@@ -33,6 +33,7 @@ struct Spec {
   int32_t out_dtype = FKL_F32;
   float fp8_scale = 1.f;
   bool vinput_u8 = false;       // vertical chain over a u8 tensor
+  int32_t in_dtype = FKL_U8;    // typed chains: element type of the inputs
   std::vector<int32_t> vkinds;  // vertical chain: 0 = Mul, 1 = Add
   std::vector<float> vconsts;
 };
@@ -80,6 +81,14 @@ cudaError_t finalize_reduce(const fkl::ReduceAcc* acc, double count, float* stat
 constexpr int kVChainCap = 4096;
 cudaError_t launch_vchain(const Spec& s, const fkl_launch_shape& shape, const void* in, float* out,
                           int64_t n, cudaStream_t stream);
+
+// Typed chains (k_cast.cu): n linear tensors of `len` elements each into
+// out[n * len]; fused (one launch per 256 tensors) and unfused (one kernel
+// per op and tensor, in place on the output).
+cudaError_t launch_cast(const Spec& s, const fkl_launch_shape& shape, int n, const void* const* ins, void* out,
+                        int64_t len, cudaStream_t stream);
+cudaError_t launch_unfused_cast(const Spec& s, int n, const void* const* ins, void* out, int64_t len,
+                                cudaStream_t stream);
 
 // Unfused reference form (k_unfused.cu): one kernel per op for one image;
 // ws0 and ws1 each hold one intermediate image.

@@ -20,7 +20,7 @@ LIB_PATH = os.path.join(_HERE, "libfkl.so")
 # status codes
 FKL_OK, FKL_ERR_INVALID, FKL_ERR_UNSUPPORTED, FKL_ERR_OOM, FKL_ERR_CUDA, FKL_ERR_TIMEOUT = range(6)
 # element types
-FKL_U8, FKL_F32, FKL_F16, FKL_BF16, FKL_E4M3 = range(5)
+FKL_U8, FKL_F32, FKL_F16, FKL_BF16, FKL_E4M3, FKL_U16, FKL_F64 = range(7)
 # layouts
 FKL_LAYOUT_LINEAR, FKL_LAYOUT_HWC, FKL_LAYOUT_NV12, FKL_LAYOUT_NCHW, FKL_LAYOUT_NHWC = range(5)
 # op codes
@@ -28,6 +28,8 @@ FKL_OP_READ_U8C3 = 1
 FKL_OP_READ_NV12 = 2
 FKL_OP_READ_F32 = 3
 FKL_OP_READ_U8 = 4
+FKL_OP_READ_U16 = 5
+FKL_OP_READ_F64 = 6
 FKL_OP_CROP = 10
 FKL_OP_RESIZE = 11
 FKL_OP_LETTERBOX = 12
@@ -213,6 +215,19 @@ def read_u8():
     return _desc(FKL_OP_READ_U8)
 
 
+def read_u16():
+    return _desc(FKL_OP_READ_U16)
+
+
+def read_f64():
+    return _desc(FKL_OP_READ_F64)
+
+
+def read_linear(dtype: int):
+    """The linear read op of an element type (typed and vertical chains)."""
+    return {FKL_U8: read_u8, FKL_U16: read_u16, FKL_F32: read_f32, FKL_F64: read_f64}[dtype]()
+
+
 def crop(x, y, w, h):
     return _desc(FKL_OP_CROP, i=(x, y, w, h))
 
@@ -274,7 +289,9 @@ def _torch():
 def dtype_code(t) -> int:
     torch = _torch()
     m = {torch.uint8: FKL_U8, torch.float32: FKL_F32, torch.float16: FKL_F16,
-         torch.bfloat16: FKL_BF16}
+         torch.bfloat16: FKL_BF16, torch.float64: FKL_F64}
+    if hasattr(torch, "uint16"):
+        m[torch.uint16] = FKL_U16
     if hasattr(torch, "float8_e4m3fn"):
         m[torch.float8_e4m3fn] = FKL_E4M3
     if t.dtype not in m:

@@ -60,6 +60,22 @@ def f32_uniform(seed: int, n: int, lo: float = -1.0, hi: float = 1.0) -> np.ndar
     return rng.uniform(lo, hi, size=n).astype(np.float32)
 
 
+def linear_values(seed: int, n: int, dtype: str) -> np.ndarray:
+    """n values of one element type for the typed chains: u8 uniform in
+    [0, 255], u16 uniform in [0, 65535], f32 and f64 uniform in [-1, 1) (the
+    f64 values carry all 53 mantissa bits, so a cast to f32 rounds)."""
+    rng = np.random.default_rng(seed)
+    if dtype == "u8":
+        return rng.integers(0, 256, size=n, dtype=np.uint8)
+    if dtype == "u16":
+        return rng.integers(0, 65536, size=n, dtype=np.uint16)
+    if dtype == "f32":
+        return rng.uniform(-1.0, 1.0, size=n).astype(np.float32)
+    if dtype == "f64":
+        return rng.uniform(-1.0, 1.0, size=n)
+    raise ValueError(f"unknown element type {dtype}")
+
+
 def chain_constants(seed: int, length: int,
                     mul_range: tuple[float, float] = (0.99, 1.01),
                     add_range: tuple[float, float] = (-0.01, 0.01)):

@@ -23,6 +23,11 @@ VCHAIN = dict(n=64 * 1024 * 1024, lengths=(1, 10, 100, 1000))
 NV12 = dict(n=256, h=720, w=1280, out=640, pad=114.0)
 # Serving: full-frame resize to 224x224, FP16 planar.
 SERVE = dict(out_w=224, out_h=224)
+# Data types (paper §VI-I): 50 matrices of 60x120, Read -> Cast -> Multiply ->
+# Subtract -> Divide -> Write, for every input type in {u8, u16, f32, f64}
+# and output (compute) type in {f32, f64}: the 8 combinations.
+DTYPES = dict(n=50, rows=60, cols=120, ins=("u8", "u16", "f32", "f64"), outs=("f32", "f64"),
+              mul=INV255, sub=0.485, div=0.229)
 
 
 def normalize_chain(out_w, out_h, out_dtype=F.FKL_F32, roi=None, scale=None, swap=True):
@@ -63,4 +68,17 @@ def integer_chain(roi=None, swap=True, add_k=(0, 0, 0), split=False):
         ops.append(F.swap_rb())
     ops.append(F.add_sat_u8(add_k))
     ops.append(F.write_split(F.FKL_U8) if split else F.write_packed(F.FKL_U8))
+    return ops
+
+
+def typed_chain(in_dtype, out_dtype, mul=None, sub=None, div=None):
+    """READ_<in> [MUL] [SUB] [DIV] WRITE_PACKED(<out>) (paper §VI-I)."""
+    ops = [F.read_linear(in_dtype)]
+    if mul is not None:
+        ops.append(F.mul(mul))
+    if sub is not None:
+        ops.append(F.sub(sub))
+    if div is not None:
+        ops.append(F.div(div))
+    ops.append(F.write_packed(out_dtype))
     return ops

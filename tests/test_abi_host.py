@@ -83,8 +83,15 @@ def test_unsupported_chains(F):
                        F.write_split(F.FKL_F32)]) == F.FKL_ERR_UNSUPPORTED
     assert _status(F, [F.read_u8c3(), F.resize(4, 4), F.write_packed(F.FKL_BF16)]) == F.FKL_ERR_UNSUPPORTED
     assert _status(F, [F.read_nv12(), F.resize(4, 4), F.add_sat_u8(3), F.write_split(F.FKL_U8)]) == F.FKL_ERR_UNSUPPORTED
-    assert _status(F, [F.read_f32(), F.div(2.0), F.write_packed(F.FKL_F32)]) == F.FKL_ERR_UNSUPPORTED
     assert _status(F, [F.read_f32(), F.mul(2.0), F.write_split(F.FKL_F32)]) == F.FKL_ERR_UNSUPPORTED
+    # typed chains: MUL, then ADD|SUB, then DIV, each at most once; F32/F64 out
+    assert _status(F, [F.read_f32(), F.div(2.0), F.mul(2.0), F.write_packed(F.FKL_F32)]) == F.FKL_ERR_UNSUPPORTED
+    assert _status(F, [F.read_u16(), F.mul(2.0), F.mul(2.0), F.write_packed(F.FKL_F32)]) == F.FKL_ERR_UNSUPPORTED
+    assert _status(F, [F.read_u16(), F.swap_rb(), F.write_packed(F.FKL_F32)]) == F.FKL_ERR_UNSUPPORTED
+    assert _status(F, [F.read_f64(), F.mul(2.0), F.write_packed(F.FKL_F16)]) == F.FKL_ERR_UNSUPPORTED
+    assert _status(F, [F.read_f64(), F.mul(2.0), F.write_packed(F.FKL_U16)]) == F.FKL_ERR_UNSUPPORTED
+    assert _status(F, [F.read_u8c3(), F.resize(4, 4), F.write_split(F.FKL_F64)]) == F.FKL_ERR_UNSUPPORTED
+    assert _status(F, [F.read_f64(), F.crop(0, 0, 2, 2), F.write_packed(F.FKL_F64)]) == F.FKL_ERR_INVALID
 
 
 def test_supported_chains_and_names(F):
@@ -96,6 +103,11 @@ def test_supported_chains_and_names(F):
         (W.vertical_chain([0, 1, 0], [1.0, 2.0, 3.0]), "ReadF32>(Mul|Add)x3>WriteF32"),
         (W.integer_chain(roi=(1, 1, 4, 4), add_k=(1, 2, 3)), "CropU8C3>SwapRB>AddSatU8>WriteU8"),
         ([F.read_u8c3(), F.crop(0, 0, 8, 8), F.mul(2.0), F.write_split(F.FKL_F32)], "ResizeU8C3>Mul"),
+        (W.typed_chain(F.FKL_U16, F.FKL_F64, 1 / 255, 0.5, 0.25), "Read<u16>>Cast<f64>>Mul>Sub>Div>Write<f64>"),
+        (W.typed_chain(F.FKL_F32, F.FKL_F32, div=3.0), "Read<f32>>Cast<f32>>Div>Write<f32>"),
+        (W.typed_chain(F.FKL_F64, F.FKL_F32), "Read<f64>>Cast<f32>>Write<f32>"),
+        ([F.read_u8(), F.mul(2.0), F.add(1.0), F.write_packed(F.FKL_F32)], "fused:ReadU8>(Mul|Add)x2"),
+        ([F.read_u8(), F.mul(2.0), F.add(1.0), F.write_packed(F.FKL_F64)], "Read<u8>>Cast<f64>>Mul>Sub"),
     ]
     for ops, frag in cases:
         p = F.fkl_pipeline_create(ops)
@@ -212,3 +224,32 @@ def test_device_wait_limit_is_validated_on_the_host(F):
     assert e.value.status == F.FKL_ERR_INVALID
     F.fkl_set_device_wait_limit(5 * 10**8)
     F.fkl_set_device_wait_limit(0)  # back to the default
+
+
+def test_typed_chain_validation(F):
+    """Typed chains check types, lengths and the output size on the host."""
+    from paper_2508_07071_gb300 import workloads as W
+    p = F.fkl_pipeline_create(W.typed_chain(F.FKL_U16, F.FKL_F64, 2.0, 1.0, 4.0))
+    try:
+        shapes = F.fkl_pipeline_shapes(p)
+        assert shapes and all(s[0] in (8, 16) and s[1] in (128, 256) for s in shapes)
+        ok = F._tensor(0x1000, (100,), 0, F.FKL_U16, F.FKL_LAYOUT_LINEAR)
+        out2 = F._tensor(0x9000, (200,), 0, F.FKL_F64, F.FKL_LAYOUT_LINEAR)
+        bad = {
+            "input dtype": ([F._tensor(0x1000, (100,), 0, F.FKL_U8, F.FKL_LAYOUT_LINEAR), ok], out2),
+            "lengths differ": ([ok, F._tensor(0x2000, (99,), 0, F.FKL_U16, F.FKL_LAYOUT_LINEAR)], out2),
+            "output dtype": ([ok, ok], F._tensor(0x9000, (200,), 0, F.FKL_F32, F.FKL_LAYOUT_LINEAR)),
+            "output size": ([ok, ok], F._tensor(0x9000, (199,), 0, F.FKL_F64, F.FKL_LAYOUT_LINEAR)),
+            "output layout": ([ok, ok], F._tensor(0x9000, (2, 100, 1, 1), 0, F.FKL_F64, F.FKL_LAYOUT_NCHW)),
+            "null input": ([ok, F._tensor(0, (100,), 0, F.FKL_U16, F.FKL_LAYOUT_LINEAR)], out2),
+        }
+        for name, (ins, o) in bad.items():
+            with pytest.raises(F.FklError) as ei:
+                F.fkl_execute_batch(p, ins, None, o, stream=0)
+            assert ei.value.status == F.FKL_ERR_INVALID, name
+        with pytest.raises(F.FklError) as ei:  # typed chains take no ROIs
+            F.fkl_execute_batch(p, [ok, ok], [(0, 0, 1, 1), (0, 0, 1, 1)], out2, stream=0)
+        assert ei.value.status == F.FKL_ERR_INVALID
+        assert F.fkl_unfused_workspace_bytes(p, [ok, ok], None, out2) == 0  # in place on the output
+    finally:
+        F.fkl_pipeline_destroy(p)

@@ -6,6 +6,7 @@ tests/golden/, or brute force on a tiny input, so that a dropped term, a wrong
 sign or index, or a transposed operand in the oracle fails at least one test.
 """
 import json
+from fractions import Fraction
 import os
 
 import numpy as np
@@ -437,3 +438,107 @@ def test_reduce_stats_closed_forms():
     np.testing.assert_allclose(st["mean"], [7.0, -3.0 / 20, 9.5])
     assert st["amax"] == 19.0 and st["scale"] == 19.0 / 448
     assert O.reduce_stats(np.zeros((3, 2, 2)))["scale"] == 1.0
+
+
+# ------------------------------------------------------------------ typed chains (§VI-I data types)
+
+def _f32_bits(v):
+    return int(np.array(v, dtype=np.float32).view(np.uint32))
+
+
+def test_typed_cast_f64_to_f32_rounds_ties_to_even():
+    # 1 + 2^-24 lies halfway between 1 and 1 + 2^-23: the even neighbour is 1.
+    # 1 + 3*2^-24 lies halfway between 1 + 2^-23 and 1 + 2^-22: the even one is 1 + 2^-22.
+    # 1 + 2^-24 + 2^-50 is just above the first midpoint: rounds up.
+    x = np.array([1 + 2.0**-24, 1 + 3 * 2.0**-24, 1 + 2.0**-24 + 2.0**-50, -(1 + 2.0**-24)])
+    y = O.typed_chain(x, "f32")
+    assert [_f32_bits(v) for v in y] == [0x3F800000, 0x3F800002, 0x3F800001, 0xBF800000]
+
+
+def test_typed_cast_integers_are_exact():
+    assert O.typed_chain(np.array([0, 65535], np.uint16), "f32").tolist() == [0.0, 65535.0]
+    assert O.typed_chain(np.array([255], np.uint8), "f64").tolist() == [255.0]
+    x = np.float32(0.1)
+    assert Fraction(float(O.typed_chain(np.array([x]), "f64")[0])) == Fraction(float(x))
+
+
+def test_typed_chain_exact_rationals_and_op_order():
+    # with mul 2, sub 1, div 4 every step is exact in binary: y = (2x - 1) / 4
+    x = np.array([0, 1, 3, 255], np.uint8)
+    for ct in ("f32", "f64"):
+        y = O.typed_chain(x, ct, mul=2, sub=1, div=4)
+        assert [Fraction(float(v)) for v in y] == [Fraction(2 * int(v) - 1, 4) for v in x]
+    # Mul before Sub: 3*2 - 1 = 5 (not 2*(3 - 1) = 4)
+    assert O.typed_chain(np.array([3], np.uint8), "f32", mul=2, sub=1)[0] == 5.0
+
+
+def test_typed_chain_constants_are_float32_values():
+    # the descriptor carries float32: a f64 chain multiplies by fl32(0.1), not 0.1
+    y = O.typed_chain(np.array([1.0]), "f64", mul=0.1)[0]
+    assert Fraction(float(y)) == Fraction(float(np.float32(0.1))) != Fraction(0.1)
+
+
+def _correctly_rounded(y, exact: Fraction, ct) -> bool:
+    """y is the ct value nearest to `exact`, ties to the even significand."""
+    y = ct(y)
+    lo, hi = np.nextafter(y, ct(-np.inf)), np.nextafter(y, ct(np.inf))
+    d = abs(Fraction(float(y)) - exact)
+    for nb in (lo, hi):
+        dn = abs(Fraction(float(nb)) - exact)
+        if dn < d:
+            return False
+        if dn == d:  # a tie: y must have the even significand
+            bits = int(np.array(y).view(np.uint32 if ct is np.float32 else np.uint64))
+            if bits & 1:
+                return False
+    return True
+
+
+@pytest.mark.parametrize("ct,name", [(np.float32, "f32"), (np.float64, "f64")])
+def test_typed_ops_are_correctly_rounded(ct, name):
+    """Each op alone equals the exact rational result rounded to nearest even
+    (checked against both neighbours with exact fractions)."""
+    rng = np.random.default_rng(7)
+    xs = rng.uniform(-4, 4, 40).astype(ct)
+    cs = [np.float32(0.3), np.float32(-1.7), np.float32(1 / 3), np.float32(2.5e-3)]
+    for c in cs:
+        C = Fraction(float(c))
+        for x in xs:
+            X = Fraction(float(x))
+            assert _correctly_rounded(O.typed_chain(np.array([x]), name, mul=c)[0], X * C, ct)
+            assert _correctly_rounded(O.typed_chain(np.array([x]), name, sub=c)[0], X - C, ct)
+            assert _correctly_rounded(O.typed_chain(np.array([x]), name, div=c)[0], X / C, ct)
+
+
+def _round_exact(q: Fraction, ct):
+    """The ct value nearest to the rational q, ties to even (brute force
+    around a first guess; independent of numpy's arithmetic)."""
+    y = ct(float(q))  # within a couple of ulps of q
+    for _ in range(4):
+        best = y
+        for nb in (np.nextafter(y, ct(-np.inf)), np.nextafter(y, ct(np.inf))):
+            dn, db = abs(Fraction(float(nb)) - q), abs(Fraction(float(best)) - q)
+            odd = int(np.array(best).view(np.uint32 if ct is np.float32 else np.uint64)) & 1
+            if dn < db or (dn == db and odd):
+                best = nb
+        if best == y:
+            return y
+        y = best
+    return y
+
+
+@pytest.mark.parametrize("src,name", [("f64", "f32"), ("u16", "f32"), ("f32", "f64"), ("u8", "f32")])
+def test_typed_chain_rounds_after_every_op(src, name):
+    """Cast, Mul, Sub, Div each rounded to the compute type in turn (an f32
+    chain evaluated in f64 and rounded once would fail here)."""
+    ct = np.float32 if name == "f32" else np.float64
+    x = synth.linear_values(5, 300, src)
+    m, s, d = np.float32(1 / 255), np.float32(0.485), np.float32(0.229)
+    y = O.typed_chain(x, name, mul=m, sub=s, div=d)
+    M, S, D = (Fraction(float(c)) for c in (m, s, d))
+    for xi, yi in zip(x, y):
+        t = _round_exact(Fraction(float(xi)), ct)
+        t = _round_exact(Fraction(float(t)) * M, ct)
+        t = _round_exact(Fraction(float(t)) - S, ct)
+        t = _round_exact(Fraction(float(t)) / D, ct)
+        assert np.array(t).tobytes() == np.array(yi, dtype=ct).tobytes(), (xi, yi, t)

@@ -644,3 +644,73 @@ def test_row_staged_wait_limit_reports_timeout_and_device_stays_usable(F, W):
     got = run_batch(F, ops, srcs, None, (64, 3, 640, 640), "bf16", layout_in=F.FKL_LAYOUT_NV12, shape=shape)
     F.fkl_device_check()
     assert torch.equal(got.view(torch.int16), base.view(torch.int16))
+
+
+# ------------------------------------------------------------------ typed chains (§VI-I data types)
+
+_TD = {"u8": "FKL_U8", "u16": "FKL_U16", "f32": "FKL_F32", "f64": "FKL_F64"}
+
+
+def _typed_run(F, ops, xs, dst, shape=None, unfused=False, offset=0):
+    """Run a typed chain over device copies of xs (views starting `offset`
+    elements in, to test unaligned pointers); returns the output on the host."""
+    dev = [torch.from_numpy(x).cuda()[offset:] for x in xs]
+    L = dev[0].numel() if dev else 0
+    out = torch.full((len(xs) * L,), float("nan"), dtype=tdtype(dst) if dst == "f32" else torch.float64,
+                     device="cuda")
+    p = F.Pipeline(ops)
+    if shape is not None:
+        F.fkl_pipeline_set_shape(p.handle, shape)
+    ins = [F.as_fkl(d) for d in dev]
+    if unfused:
+        F.fkl_execute_batch_unfused(p.handle, ins, None, F.as_fkl(out), 0, 0)
+    else:
+        F.fkl_execute_batch(p.handle, ins, None, F.as_fkl(out))
+    torch.cuda.synchronize()
+    return out.cpu().numpy()
+
+
+def _bits_equal(a, b):
+    a, b = np.ascontiguousarray(a), np.ascontiguousarray(b)
+    return a.dtype == b.dtype and a.shape == b.shape and a.tobytes() == b.tobytes()
+
+
+@pytest.mark.parametrize("src", ["u8", "u16", "f32", "f64"])
+@pytest.mark.parametrize("dst", ["f32", "f64"])
+def test_typed_chain_bit_exact_every_shape_and_unfused(F, W, src, dst):
+    cfg = W.DTYPES
+    L = cfg["rows"] * cfg["cols"]
+    xs = [synth.linear_values(100 + i, L, src) for i in range(cfg["n"])]
+    ops = W.typed_chain(getattr(F, _TD[src]), getattr(F, _TD[dst]), cfg["mul"], cfg["sub"], cfg["div"])
+    want = np.concatenate([O.typed_chain(x, dst, cfg["mul"], cfg["sub"], cfg["div"]) for x in xs])
+    p = F.Pipeline(ops)
+    for shape in F.fkl_pipeline_shapes(p.handle):
+        assert _bits_equal(_typed_run(F, ops, xs, dst, shape=shape), want), shape
+    assert _bits_equal(_typed_run(F, ops, xs, dst, unfused=True), want)
+
+
+@pytest.mark.parametrize("src,dst", [("u8", "f32"), ("u16", "f64"), ("f64", "f32"), ("f32", "f64")])
+def test_typed_chain_edges(F, W, src, dst):
+    si, di = getattr(F, _TD[src]), getattr(F, _TD[dst])
+    # ragged length and unaligned views (scalar loads and stores)
+    xs = [synth.linear_values(7 + i, 1003, src) for i in range(3)]
+    ops = W.typed_chain(si, di, 3.0, -0.5, 7.0)
+    for off in (0, 1):
+        want = np.concatenate([O.typed_chain(x[off:], dst, 3.0, -0.5, 7.0) for x in xs])
+        for shape in [(8, 128, 1, 1), (16, 256, 1, 1)]:
+            assert _bits_equal(_typed_run(F, ops, xs, dst, shape=shape, offset=off), want), (off, shape)
+    # more than 256 tensors (two launches), partial chains
+    xs = [synth.linear_values(300 + i, 40, src) for i in range(300)]
+    for kw in [dict(div=3.0), dict(mul=0.1), dict(sub=2.0), {}]:
+        ops = W.typed_chain(si, di, **kw)
+        want = np.concatenate([O.typed_chain(x, dst, **kw) for x in xs])
+        assert _bits_equal(_typed_run(F, ops, xs, dst), want), kw
+        assert _bits_equal(_typed_run(F, ops, xs, dst, unfused=True), want), kw
+    # empty batch and empty tensors are no-ops
+    p = F.Pipeline(W.typed_chain(si, di, 2.0))
+    out = torch.zeros(4, dtype=torch.float64 if dst == "f64" else torch.float32, device="cuda")
+    F.fkl_execute_batch(p.handle, [], None, F.as_fkl(out[:0]))
+    e = torch.from_numpy(synth.linear_values(1, 4, src)).cuda()[:0]
+    F.fkl_execute_batch(p.handle, [F.as_fkl(e)], None, F.as_fkl(out[:0]))
+    torch.cuda.synchronize()
+    assert float(out.abs().sum()) == 0.0
