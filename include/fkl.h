@@ -147,12 +147,15 @@ typedef struct fkl_pipeline_s* fkl_pipeline;  /* library-owned handle        */
  *   READ_NV12 (RESIZE|LETTERBOX) [SWAP_RB] [MUL] [ADD|SUB] [DIV] WRITE_{SPLIT,PACKED}
  *   READ_U8C3 [CROP] [SWAP_RB] [ADD_SAT_U8] WRITE_{SPLIT,PACKED} (U8 output)
  *   READ_F32|READ_U8 (MUL|ADD){0..65536} WRITE_PACKED(F32)   (vertical chain)
- *   READ_U8|READ_U16|READ_F32|READ_F64 [MUL] [ADD|SUB] [DIV] WRITE_PACKED(F32|F64)
+ *   READ_U8|READ_U16|READ_F32|READ_F64 [MUL] [ADD|SUB] [DIV]
+ *        WRITE_PACKED(F32|F64|F16|BF16|E4M3)
  *        (typed chain, paper §VI-I Read -> Cast -> Multiply -> Subtract ->
- *        Divide -> Write: the input is cast to the output type, then every
- *        op runs and rounds once in the output type, constants f[0] taken
- *        exactly into it; a READ_F32|READ_U8 chain of MUL/ADD only writing
- *        F32 is a vertical chain)
+ *        Divide -> Write: the input is cast to the compute type -- F64 for an
+ *        F64 output, else F32 -- then every op runs and rounds once in it,
+ *        constants f[0] taken exactly into it; the write rounds to the output
+ *        type to nearest even (E4M3: the F32 product with fl32(1/s) is rounded,
+ *        saturating at +-448). A READ_F32|READ_U8 chain of MUL/ADD only
+ *        writing F32 is a vertical chain)
  * An absent MUL/ADD/SUB/DIV is bound as its identity (x*1, x-0, x/1 are
  * exact, so the result equals the shorter chain bit for bit). A chain of the
  * right grammar outside this set returns FKL_ERR_UNSUPPORTED.
@@ -217,9 +220,11 @@ FKL_API const char* fkl_last_error(void);
  * device memory that fusion saves (paper §VI-L).
  * fkl_execute_batch_unfused: `workspace` is caller-owned device memory of at
  * least that size, 256-byte aligned. Launch count = n * (ops in the chain).
- * Tensor chains (vertical and typed) need no workspace (0 bytes; each op
- * runs in place on the output): one kernel per tensor and op (for typed
- * chains the first kernel reads, casts and writes the output).
+ * Tensor chains (vertical and typed): one kernel per tensor and op, in place
+ * on the output (0 bytes of workspace); for typed chains the first kernel
+ * reads and casts, and F16/BF16/E4M3 outputs keep the F32 values of one
+ * tensor in the workspace (its length x 4 bytes, rounded up to 256) and
+ * write the output in a last kernel per tensor.
  */
 FKL_API fkl_status fkl_unfused_workspace_bytes(fkl_pipeline p, int32_t n,
                                        const fkl_tensor* ins,

@@ -233,9 +233,16 @@ def round_bf16(x: np.ndarray) -> np.ndarray:
     return _round_to_grid(x, 7, -126)
 
 
+F16_OVERFLOW = 65520.0  # halfway between 65504 (the largest finite) and 2**16
+
+
 def round_f16(x: np.ndarray) -> np.ndarray:
-    """IEEE binary16 (5 exponent bits, 10 fraction bits), RNE, subnormals."""
-    return _round_to_grid(x, 10, -14)
+    """IEEE binary16 (5 exponent bits, 10 fraction bits), RNE, subnormals;
+    |x| >= 65520 overflows to +-inf (the tie at 65520 goes to the even
+    neighbour 2**16, which is out of range)."""
+    x = np.asarray(x, dtype=np.float64)
+    r = _round_to_grid(x, 10, -14)
+    return np.where(np.abs(x) >= F16_OVERFLOW, np.copysign(np.inf, x), r)
 
 
 E4M3_MAX = 448.0
@@ -308,18 +315,22 @@ def vertical_chain_f32(x: np.ndarray, kinds, consts) -> np.ndarray:
 _TYPES = {"u8": np.uint8, "u16": np.uint16, "f32": np.float32, "f64": np.float64}
 
 
-def typed_chain(x: np.ndarray, out_dtype: str, mul=None, sub=None, div=None) -> np.ndarray:
+def typed_chain(x: np.ndarray, out_dtype: str, mul=None, sub=None, div=None, scale=None) -> np.ndarray:
     """Read -> Cast -> Multiply -> Subtract -> Divide -> Write (§VI-I).
 
-    The input is cast to the output type (numpy's cast: exact for u8, u16 and
-    f32 into f32 or f64; round to nearest even for f64 into f32); then each
-    present op is one numpy operation in that type, rounded to it before the
-    next op reads it. The constants are float32 values (what a descriptor
-    carries) taken exactly into the output type. An absent op is skipped.
+    The input is cast to the compute type -- float64 for an f64 output,
+    float32 otherwise -- (numpy's cast: exact for u8, u16 and f32; round to
+    nearest even for f64 into f32); then each present op is one numpy
+    operation in that type, rounded to it before the next op reads it. The
+    constants are float32 values (what a descriptor carries) taken exactly
+    into the compute type. An absent op is skipped. The write rounds to the
+    output type: f16 and bf16 round to nearest even (returned as float64
+    values); e4m3 first multiplies by the float32 value of 1/scale (one
+    float32 rounding), then rounds to nearest even with saturation.
     """
-    ct = _TYPES[out_dtype]
-    if ct not in (np.float32, np.float64):
-        raise ValueError("typed chains write f32 or f64")
+    if out_dtype not in ("f32", "f64", "f16", "bf16", "e4m3"):
+        raise ValueError("typed chains write f32, f64, f16, bf16 or e4m3")
+    ct = np.float64 if out_dtype == "f64" else np.float32
     y = np.asarray(x).astype(ct)
     if mul is not None:
         y = np.multiply(y, ct(np.float32(mul)), dtype=ct)
@@ -327,6 +338,13 @@ def typed_chain(x: np.ndarray, out_dtype: str, mul=None, sub=None, div=None) -> 
         y = np.subtract(y, ct(np.float32(sub)), dtype=ct)
     if div is not None:
         y = np.divide(y, ct(np.float32(div)), dtype=ct)
+    if out_dtype == "bf16":
+        return round_bf16(y)
+    if out_dtype == "f16":
+        return round_f16(y)
+    if out_dtype == "e4m3":
+        inv = np.float32(1.0 / float(np.float32(scale)))
+        return round_e4m3(np.multiply(y, inv, dtype=np.float32))
     return y
 
 

@@ -90,8 +90,8 @@ fkl_status parse_typed(const fkl_op_desc* ops, int n, int src, Spec& s) {
   s.family = FAM_CAST;
   s.in_dtype = src == FKL_OP_READ_U8 ? FKL_U8 : src == FKL_OP_READ_U16 ? FKL_U16
                : src == FKL_OP_READ_F32 ? FKL_F32 : FKL_F64;
-  if (ops[n - 1].op != FKL_OP_WRITE_PACKED || (s.out_dtype != FKL_F32 && s.out_dtype != FKL_F64))
-    return fail(FKL_ERR_UNSUPPORTED, "typed tensor chains write packed F32 or F64");
+  if (ops[n - 1].op != FKL_OP_WRITE_PACKED || s.out_dtype == FKL_U8 || s.out_dtype == FKL_U16)
+    return fail(FKL_ERR_UNSUPPORTED, "typed tensor chains write packed F32, F64, F16, BF16 or E4M3");
   int stage = 0;  // compiled order: MUL, ADD|SUB, DIV
   for (int k = 1; k < n - 1; ++k) {
     const fkl_op_desc& d = ops[k];
@@ -590,19 +590,30 @@ fkl_status check_linear(const Spec& s, int32_t n, const fkl_tensor* ins, const i
   return FKL_OK;
 }
 
+// Device workspace of the unfused form of a tensor chain: a float32 copy of
+// one tensor for typed chains writing F16/BF16/E4M3, nothing otherwise.
+size_t linear_workspace_bytes(const Spec& s, int64_t len) {
+  const bool narrow = s.family == FAM_CAST && s.out_dtype != FKL_F32 && s.out_dtype != FKL_F64;
+  return narrow ? static_cast<size_t>((len * 4 + 255) / 256 * 256) : 0;
+}
+
 // Runs a tensor chain: typed chains in one launch per 256 tensors, vertical
-// chains one launch per tensor (and per 4096 ops); unfused: one kernel per op.
+// chains one launch per tensor (and per 4096 ops); unfused: one kernel per op,
+// with `ws` (linear_workspace_bytes) when the chain needs one.
 fkl_status run_linear(fkl_pipeline p, int32_t n, const fkl_tensor* ins, const int32_t* rois, fkl_tensor* out,
-                      bool unfused, void* stream) {
+                      bool unfused, void* stream, void* ws = nullptr, size_t ws_bytes = 0) {
   int64_t len = 0;
   std::vector<const void*> ptrs;
   const fkl_status st = check_linear(p->spec, n, ins, rois, out, len, ptrs);
   if (st != FKL_OK) return st;
   if (n == 0 || len == 0) return FKL_OK;
+  const size_t need = unfused ? linear_workspace_bytes(p->spec, len) : 0;
+  if (need && (!ws || ws_bytes < need || reinterpret_cast<uintptr_t>(ws) % 256))
+    return fail(FKL_ERR_INVALID, "workspace must be >= %zu bytes and 256-byte aligned", need);
   const cudaStream_t cs = static_cast<cudaStream_t>(stream);
   cudaError_t e = cudaSuccess;
   if (p->spec.family == FAM_CAST) {
-    e = unfused ? launch_unfused_cast(p->spec, n, ptrs.data(), out->data, len, cs)
+    e = unfused ? launch_unfused_cast(p->spec, n, ptrs.data(), out->data, len, ws, cs)
                 : launch_cast(p->spec, p->shape, n, ptrs.data(), out->data, len, cs);
   } else {
     for (int i = 0; i < n && e == cudaSuccess; ++i) {
@@ -782,7 +793,14 @@ fkl_status fkl_unfused_workspace_bytes(fkl_pipeline p, int32_t n, const fkl_tens
   if (!bytes) return fail(FKL_ERR_INVALID, "bytes is NULL");
   *bytes = 0;
   if (!p) return fail(FKL_ERR_INVALID, "null pipeline");
-  if (p->spec.family == FAM_VCHAIN || p->spec.family == FAM_CAST) return FKL_OK;  // in place on `out`
+  if (is_tensor_chain(p->spec)) {
+    int64_t len = 0;
+    std::vector<const void*> ptrs;
+    const fkl_status st = check_linear(p->spec, n, ins, rois, out, len, ptrs);
+    if (st != FKL_OK) return st;
+    *bytes = linear_workspace_bytes(p->spec, len);
+    return FKL_OK;
+  }
   OutDesc od;
   std::vector<fkl::ResampleParams> imgs;
   const fkl_status st = validate_batch(p, n, ins, rois, out, od, imgs);
@@ -800,7 +818,7 @@ fkl_status fkl_execute_batch_unfused(fkl_pipeline p, int32_t n, const fkl_tensor
                                      fkl_tensor* out, void* workspace, size_t workspace_bytes, void* stream) {
   if (!p) return fail(FKL_ERR_INVALID, "null pipeline");
   const cudaStream_t s = static_cast<cudaStream_t>(stream);
-  if (is_tensor_chain(p->spec)) return run_linear(p, n, ins, rois, out, true, stream);  // in place: no scratch
+  if (is_tensor_chain(p->spec)) return run_linear(p, n, ins, rois, out, true, stream, workspace, workspace_bytes);
   size_t need = 0;
   fkl_status st = fkl_unfused_workspace_bytes(p, n, ins, rois, out, &need);
   if (st != FKL_OK) return st;
@@ -917,7 +935,12 @@ fkl_status fkl_execute_batch_unfused_static(fkl_pipeline p, int32_t n, const fkl
                                             fkl_tensor* out, void* stream) {
   if (!p) return fail(FKL_ERR_INVALID, "null pipeline");
   const cudaStream_t s = static_cast<cudaStream_t>(stream);
-  if (is_tensor_chain(p->spec)) return run_linear(p, n, ins, rois, out, true, stream);  // in place: no scratch
+  if (is_tensor_chain(p->spec)) {  // the float32 copy of one tensor, if any, lives in the static scratch
+    void* scratch = nullptr;
+    const cudaError_t e = static_scratch(&scratch);
+    if (e != cudaSuccess) return cuda_fail(e, "static scratch lookup");
+    return run_linear(p, n, ins, rois, out, true, stream, scratch, kStaticScratchBytes);
+  }
   if (n < 0) return fail(FKL_ERR_INVALID, "negative batch size");
   if (n > 0 && !ins) return fail(FKL_ERR_INVALID, "inputs missing");
   OutDesc od;

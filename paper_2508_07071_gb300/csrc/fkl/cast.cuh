@@ -1,9 +1,12 @@
 // Typed chains (paper §VI-I, the data-type experiment): Read -> Cast ->
 // Multiply -> Subtract -> Divide -> Write over a batch of linear tensors.
-// The input element is cast to the compute type CT (the output type), then
-// each present op runs once in CT with IEEE round-to-nearest-even; absent
-// ops are skipped (a uniform branch). One thread handles E consecutive
-// elements of one tensor; blockIdx.y is the tensor (horizontal fusion).
+// The input element is cast to the compute type CT (float64 for a float64
+// output, float32 otherwise), then each present op runs once in CT with IEEE
+// round-to-nearest-even; absent ops are skipped (a uniform branch). The
+// write rounds to the output type (FP8: the float32 product with fl32(1/s)
+// first, then round-to-nearest-even with saturation). One thread handles E
+// consecutive elements of one tensor; blockIdx.y is the tensor (horizontal
+// fusion).
 #pragma once
 
 #include "core.cuh"
@@ -18,8 +21,17 @@ struct CastArgs {
   int64_t len;               // elements per tensor
   int32_t n;                 // tensors in this launch
   int32_t has_mul, has_sub, has_div;
-  int32_t _pad;
+  float scale_inv;           // FP8 output: fl32(1 / s)
   double mul, sub, div;      // constants; each float converts exactly to CT
+};
+
+template <class OutT>
+struct CastCompute {
+  using type = float;
+};
+template <>
+struct CastCompute<double> {
+  using type = double;
 };
 
 template <class InT, class CT>
@@ -76,17 +88,16 @@ FKL_D void store_run_linear(T* p, bool vec, int n, const T (&x)[E]) {
     if (k < n) p[k] = x[k];
 }
 
-template <class InT, class CT, int E>
+template <class InT, class OutT, int E>
 __global__ void __launch_bounds__(256) cast_chain_kernel(const __grid_constant__ CastArgs a) {
+  using CT = typename CastCompute<OutT>::type;
   const int z = blockIdx.y;
   const int64_t i0 = (static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x) * E;
   if (z >= a.n || i0 >= a.len) return;
   const int n = a.len - i0 < E ? static_cast<int>(a.len - i0) : E;
   const InT* src = static_cast<const InT*>(a.in[z]) + i0;
-  CT* dst = static_cast<CT*>(a.out) + static_cast<int64_t>(z) * a.len + i0;
   constexpr uintptr_t kInVec = E * sizeof(InT) >= 16 ? 16 : E * sizeof(InT);
   const bool vin = n == E && reinterpret_cast<uintptr_t>(src) % kInVec == 0;
-  const bool vout = n == E && reinterpret_cast<uintptr_t>(dst) % 16 == 0;
   InT v[E];
   load_run<InT, E>(src, vin, n, v);
   const CT m = static_cast<CT>(a.mul), s = static_cast<CT>(a.sub), d = static_cast<CT>(a.div);
@@ -99,7 +110,25 @@ __global__ void __launch_bounds__(256) cast_chain_kernel(const __grid_constant__
     if (a.has_div) t = div_rn(t, d);
     x[k] = t;
   }
-  store_run_linear<CT, E>(dst, vout, n, x);
+  if constexpr (std::is_same_v<OutT, double>) {
+    double* dst = static_cast<double*>(a.out) + static_cast<int64_t>(z) * a.len + i0;
+    store_run_linear<double, E>(dst, n == E && reinterpret_cast<uintptr_t>(dst) % 16 == 0, n, x);
+  } else {
+    constexpr int B = Format<OutT>::bytes;
+    uint8_t* q = static_cast<uint8_t*>(a.out) + (static_cast<int64_t>(z) * a.len + i0) * B;
+    if constexpr (std::is_same_v<OutT, e4m3_t>) {
+#pragma unroll
+      for (int k = 0; k < E; ++k) x[k] = __fmul_rn(x[k], a.scale_inv);
+    }
+    constexpr uintptr_t kOutVec = E * B >= 16 ? 16 : E * B;
+    if (n == E && reinterpret_cast<uintptr_t>(q) % kOutVec == 0) {
+      store_run<OutT, E>(q, x);
+    } else {
+#pragma unroll
+      for (int k = 0; k < E; ++k)
+        if (k < n) store_one<OutT>(q + k * B, x[k]);
+    }
+  }
 }
 
 }  // namespace fkl

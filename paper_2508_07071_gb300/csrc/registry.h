@@ -84,10 +84,11 @@ cudaError_t launch_vchain(const Spec& s, const fkl_launch_shape& shape, const vo
 
 // Typed chains (k_cast.cu): n linear tensors of `len` elements each into
 // out[n * len]; fused (one launch per 256 tensors) and unfused (one kernel
-// per op and tensor, in place on the output).
+// per op and tensor, in place on a float32/float64 output, else on `ws`:
+// len float32 values).
 cudaError_t launch_cast(const Spec& s, const fkl_launch_shape& shape, int n, const void* const* ins, void* out,
                         int64_t len, cudaStream_t stream);
-cudaError_t launch_unfused_cast(const Spec& s, int n, const void* const* ins, void* out, int64_t len,
+cudaError_t launch_unfused_cast(const Spec& s, int n, const void* const* ins, void* out, int64_t len, void* ws,
                                 cudaStream_t stream);
 
 // Unfused reference form (k_unfused.cu): one kernel per op for one image;

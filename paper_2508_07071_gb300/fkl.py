@@ -269,8 +269,8 @@ def write_split(dtype: int, scale: float | None = None):
     return _desc(FKL_OP_WRITE_SPLIT, f=(scale,) if scale is not None else (), i=(dtype,))
 
 
-def write_packed(dtype: int):
-    return _desc(FKL_OP_WRITE_PACKED, i=(dtype,))
+def write_packed(dtype: int, scale: float | None = None):
+    return _desc(FKL_OP_WRITE_PACKED, f=(scale,) if scale is not None else (), i=(dtype,))
 
 
 def scalar_op(op: int, c: float) -> fkl_op_desc:

@@ -71,8 +71,9 @@ def integer_chain(roi=None, swap=True, add_k=(0, 0, 0), split=False):
     return ops
 
 
-def typed_chain(in_dtype, out_dtype, mul=None, sub=None, div=None):
-    """READ_<in> [MUL] [SUB] [DIV] WRITE_PACKED(<out>) (paper §VI-I)."""
+def typed_chain(in_dtype, out_dtype, mul=None, sub=None, div=None, scale=None):
+    """READ_<in> [MUL] [SUB] [DIV] WRITE_PACKED(<out>) (paper §VI-I); `scale`
+    is the per-tensor scale of an E4M3 output."""
     ops = [F.read_linear(in_dtype)]
     if mul is not None:
         ops.append(F.mul(mul))
@@ -80,5 +81,5 @@ def typed_chain(in_dtype, out_dtype, mul=None, sub=None, div=None):
         ops.append(F.sub(sub))
     if div is not None:
         ops.append(F.div(div))
-    ops.append(F.write_packed(out_dtype))
+    ops.append(F.write_packed(out_dtype, scale))
     return ops

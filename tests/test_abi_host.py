@@ -88,7 +88,7 @@ def test_unsupported_chains(F):
     assert _status(F, [F.read_f32(), F.div(2.0), F.mul(2.0), F.write_packed(F.FKL_F32)]) == F.FKL_ERR_UNSUPPORTED
     assert _status(F, [F.read_u16(), F.mul(2.0), F.mul(2.0), F.write_packed(F.FKL_F32)]) == F.FKL_ERR_UNSUPPORTED
     assert _status(F, [F.read_u16(), F.swap_rb(), F.write_packed(F.FKL_F32)]) == F.FKL_ERR_UNSUPPORTED
-    assert _status(F, [F.read_f64(), F.mul(2.0), F.write_packed(F.FKL_F16)]) == F.FKL_ERR_UNSUPPORTED
+    assert _status(F, [F.read_f64(), F.mul(2.0), F.write_split(F.FKL_F16)]) == F.FKL_ERR_UNSUPPORTED
     assert _status(F, [F.read_f64(), F.mul(2.0), F.write_packed(F.FKL_U16)]) == F.FKL_ERR_UNSUPPORTED
     assert _status(F, [F.read_u8c3(), F.resize(4, 4), F.write_split(F.FKL_F64)]) == F.FKL_ERR_UNSUPPORTED
     assert _status(F, [F.read_f64(), F.crop(0, 0, 2, 2), F.write_packed(F.FKL_F64)]) == F.FKL_ERR_INVALID
@@ -251,5 +251,30 @@ def test_typed_chain_validation(F):
             F.fkl_execute_batch(p, [ok, ok], [(0, 0, 1, 1), (0, 0, 1, 1)], out2, stream=0)
         assert ei.value.status == F.FKL_ERR_INVALID
         assert F.fkl_unfused_workspace_bytes(p, [ok, ok], None, out2) == 0  # in place on the output
+    finally:
+        F.fkl_pipeline_destroy(p)
+
+
+def test_typed_chain_narrow_outputs_parse(F):
+    from paper_2508_07071_gb300 import workloads as W
+    for dt, name in [(F.FKL_BF16, "bf16"), (F.FKL_F16, "f16")]:
+        p = F.fkl_pipeline_create(W.typed_chain(F.FKL_U16, dt, 2.0))
+        try:
+            assert F.fkl_pipeline_kernel_name(p).endswith(f"Write<{name}>")
+        finally:
+            F.fkl_pipeline_destroy(p)
+    # FP8 needs its scale; packed u8/u16 outputs are not compiled
+    assert _status(F, W.typed_chain(F.FKL_F32, F.FKL_E4M3, 2.0)) == F.FKL_ERR_INVALID
+    assert _status(F, W.typed_chain(F.FKL_F32, F.FKL_E4M3, 2.0, scale=0.5)) == F.FKL_OK
+    assert _status(F, W.typed_chain(F.FKL_F32, F.FKL_U8, 2.0)) == F.FKL_ERR_UNSUPPORTED
+    assert _status(F, W.typed_chain(F.FKL_F32, F.FKL_U16, 2.0)) == F.FKL_ERR_UNSUPPORTED
+    p = F.fkl_pipeline_create(W.typed_chain(F.FKL_F64, F.FKL_BF16, 2.0))
+    try:  # the unfused form keeps one tensor's float32 values in the workspace
+        a = F._tensor(0x1000, (1000,), 0, F.FKL_F64, F.FKL_LAYOUT_LINEAR)
+        o = F._tensor(0x9000, (3000,), 0, F.FKL_BF16, F.FKL_LAYOUT_LINEAR)
+        assert F.fkl_unfused_workspace_bytes(p, [a, a, a], None, o) == 4096
+        with pytest.raises(F.FklError) as ei:
+            F.fkl_execute_batch_unfused(p, [a, a, a], None, o, 0x100000, 1024, stream=0)
+        assert ei.value.status == F.FKL_ERR_INVALID
     finally:
         F.fkl_pipeline_destroy(p)

@@ -542,3 +542,31 @@ def test_typed_chain_rounds_after_every_op(src, name):
         t = _round_exact(Fraction(float(t)) - S, ct)
         t = _round_exact(Fraction(float(t)) / D, ct)
         assert np.array(t).tobytes() == np.array(yi, dtype=ct).tobytes(), (xi, yi, t)
+
+
+def test_f16_overflow_matches_numpy_half():
+    x = np.array([65504.0, 65519.99, 65520.0, 70000.0, -65520.0, 1e9, -65519.0])
+    want = np.array(x, dtype=np.float64).astype(np.float16).astype(np.float64)
+    got = O.round_f16(x)
+    assert np.array_equal(got, want), (got, want)
+    assert np.isinf(got[2]) and got[1] == 65504.0
+
+
+def test_typed_chain_narrow_outputs_against_torch():
+    """16-bit and FP8 writes equal an independent library's conversion of the
+    float32 chain (torch's bf16 / f16 / float8_e4m3fn casts round to nearest
+    even and, for FP8, saturate)."""
+    x = synth.linear_values(9, 5000, "u16")
+    y32 = O.typed_chain(x, "f32", mul=1 / 255, sub=100.0, div=0.229)
+    t = torch.from_numpy(y32)
+    assert np.array_equal(O.typed_chain(x, "bf16", 1 / 255, 100.0, 0.229),
+                          t.to(torch.bfloat16).double().numpy())
+    assert np.array_equal(O.typed_chain(x, "f16", 1 / 255, 100.0, 0.229),
+                          t.to(torch.float16).double().numpy())
+    if hasattr(torch, "float8_e4m3fn"):
+        s = 0.75  # 1/s = 4/3 is not a float32: the product rounds once, then to E4M3
+        inv = np.float32(1.0 / np.float32(s))
+        prod = torch.from_numpy(np.multiply(y32, inv, dtype=np.float32))
+        sat = prod.clamp(-448.0, 448.0)  # torch's cast maps overflow to NaN; the write saturates
+        assert np.array_equal(O.typed_chain(x, "e4m3", 1 / 255, 100.0, 0.229, scale=s),
+                              sat.to(torch.float8_e4m3fn).double().numpy())

@@ -714,3 +714,73 @@ def test_typed_chain_edges(F, W, src, dst):
     F.fkl_execute_batch(p.handle, [F.as_fkl(e)], None, F.as_fkl(out[:0]))
     torch.cuda.synchronize()
     assert float(out.abs().sum()) == 0.0
+
+
+def _decode(F, t, fmt):
+    """Values of a device tensor of bf16 / f16 / e4m3 codes as float64 (host)."""
+    if fmt == "bf16":
+        b = t.view(torch.int16).cpu().numpy().astype(np.uint16).astype(np.uint32) << 16
+        return b.view(np.float32).astype(np.float64)
+    if fmt == "f16":
+        return t.view(torch.int16).cpu().numpy().view(np.float16).astype(np.float64)
+    return O.decode_e4m3(t.view(torch.uint8).cpu().numpy())
+
+
+_NARROW = {"bf16": (torch.bfloat16, "FKL_BF16"), "f16": (torch.float16, "FKL_F16"),
+           "e4m3": (getattr(torch, "float8_e4m3fn", None), "FKL_E4M3")}
+
+
+@pytest.mark.parametrize("src", ["u8", "u16", "f64"])
+@pytest.mark.parametrize("dst", ["bf16", "f16", "e4m3"])
+def test_typed_chain_narrow_outputs_bit_exact(F, W, src, dst):
+    tdt, code_name = _NARROW[dst]
+    scale = 0.75 if dst == "e4m3" else None
+    ops = W.typed_chain(getattr(F, _TD[src]), getattr(F, code_name), 1 / 255, 100.0, 0.229, scale=scale)
+    xs = [synth.linear_values(60 + i, 2001, src) for i in range(5)]
+    want = np.concatenate([O.typed_chain(x, dst, 1 / 255, 100.0, 0.229, scale=scale) for x in xs])
+    dev = [torch.from_numpy(x).cuda() for x in xs]
+    ins = [F.as_fkl(d) for d in dev]
+    p = F.Pipeline(ops)
+    out = torch.zeros(5 * 2001, dtype=tdt, device="cuda")
+    for shape in F.fkl_pipeline_shapes(p.handle):
+        F.fkl_pipeline_set_shape(p.handle, shape)
+        F.fkl_execute_batch(p.handle, ins, None, F.as_fkl(out))
+        torch.cuda.synchronize()
+        assert np.array_equal(_decode(F, out, dst), want), shape
+    for static in (False, True):  # unfused: a float32 workspace, or the static scratch
+        out.zero_()
+        if static:
+            F.fkl_execute_batch_unfused_static(p.handle, ins, None, F.as_fkl(out))
+        else:
+            nb = F.fkl_unfused_workspace_bytes(p.handle, ins, None, F.as_fkl(out))
+            assert nb >= 2001 * 4
+            ws = torch.empty(nb, dtype=torch.uint8, device="cuda")
+            F.fkl_execute_batch_unfused(p.handle, ins, None, F.as_fkl(out), ws.data_ptr(), nb)
+        torch.cuda.synchronize()
+        assert np.array_equal(_decode(F, out, dst), want), static
+
+
+@pytest.mark.slow
+@pytest.mark.parametrize("dst", ["bf16", "f16", "e4m3"])
+def test_device_cast_exhaustive_over_0_to_448(F, W, dst):
+    """Every float32 bit pattern in [0, 448] (0x00000000 .. 0x43E00000), cast
+    on the GPU by the write of a typed chain, equals the oracle's rounding
+    written from the format definitions (round to nearest even; FP8 with
+    scale 1 saturates at 448)."""
+    tdt, code_name = _NARROW[dst]
+    ops = [F.read_f32(), F.write_packed(getattr(F, code_name), 1.0 if dst == "e4m3" else None)]
+    p = F.Pipeline(ops)
+    last, chunk = 0x43E00000, 1 << 25
+    rnd = {"bf16": O.round_bf16, "f16": O.round_f16, "e4m3": O.round_e4m3}[dst]
+    out = torch.empty(chunk, dtype=tdt, device="cuda")
+    for start in range(0, last + 1, chunk):
+        end = min(start + chunk, last + 1)
+        x = torch.arange(start, end, dtype=torch.int64, device="cuda").to(torch.int32).view(torch.float32)
+        o = out[:end - start]
+        F.fkl_execute_batch(p.handle, [F.as_fkl(x)], None, F.as_fkl(o))
+        torch.cuda.synchronize()
+        host = np.arange(start, end, dtype=np.uint32).view(np.float32)
+        want = rnd(host.astype(np.float64))
+        got = _decode(F, o, dst)
+        bad = np.nonzero(got != want)[0]
+        assert bad.size == 0, (dst, hex(start + int(bad[0])), got[bad[0]], want[bad[0]])
