@@ -10,6 +10,7 @@
 #include <new>
 #include <string>
 
+#include "fkl/reduce.cuh"
 #include "registry.h"
 
 namespace fkl_impl {

@@ -23,6 +23,10 @@
 
 namespace fkl {
 
+// Images per launch of the batched image kernels: the capacity of their
+// per-image parameter table (horizontal fusion, paper §IV-B BatchRead).
+constexpr int kBatchCap = 256;
+
 // ---------------------------------------------------------------------------
 // Instance types (static reflection tags, paper §IV-C)
 // ---------------------------------------------------------------------------

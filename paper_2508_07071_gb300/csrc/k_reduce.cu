@@ -3,6 +3,7 @@
 #include <cstring>
 
 #include "float_family.cuh"
+#include "fkl/reduce.cuh"
 
 namespace fkl_impl {
 

@@ -4,6 +4,7 @@
 #include <algorithm>
 #include <cstring>
 
+#include "fkl/vchain.cuh"
 #include "registry.h"
 
 namespace fkl_impl {

@@ -9,6 +9,10 @@
 #include "../../include/fkl.h"
 #include "fkl/dpp.cuh"
 
+namespace fkl {
+struct ReduceAcc;  // fkl/reduce.cuh
+}  // namespace fkl
+
 namespace fkl_impl {
 
 enum Family { FAM_PACKED = 1, FAM_NV12 = 2, FAM_INT = 3, FAM_VCHAIN = 4, FAM_CAST = 5 };
@@ -39,7 +43,7 @@ struct Spec {
 };
 
 // One launch of an image family: up to kBatchCap images.
-constexpr int kBatchCap = 256;
+using fkl::kBatchCap;
 
 struct LaunchCtx {
   const Spec* spec;

@@ -50,6 +50,49 @@ def out_bytes(n, h, w, bytes_per_el, channels=3) -> int:
     return int(n * h * w * channels * bytes_per_el)
 
 
+SECTOR = 32  # bytes per DRAM sector
+
+
+def _row_sectors(starts: np.ndarray, offsets: np.ndarray) -> int:
+    """32-byte sectors touched by bytes `offsets` of rows starting at `starts`
+    (row starts are absolute byte addresses from a 32-byte aligned base)."""
+    total = 0
+    for st in np.asarray(starts, dtype=np.int64):
+        total += len(np.unique((st + offsets) // SECTOR))
+    return total
+
+
+def packed_tap_sector_bytes(rx, ry, rw, rh, dw, dh, pitch) -> int:
+    """Sector-level source footprint of one crop's bilinear taps in a packed
+    3-channel u8 image (base 32-byte aligned, `pitch` bytes per row)."""
+    xs = _axis_taps(rw, dw) + rx
+    cols = (3 * xs[:, None] + np.arange(3)[None, :]).ravel()
+    rows = (_axis_taps(rh, dh) + ry) * int(pitch)
+    return SECTOR * _row_sectors(rows, cols)
+
+
+def nv12_tap_sector_bytes(rx, ry, rw, rh, dw, dh, pitch, height) -> int:
+    """Sector-level footprint of the NV12 taps: luma rows, then the chroma
+    plane (U, V pairs) starting `height` rows after the luma base."""
+    xs = _axis_taps(rw, dw) + rx
+    ys = _axis_taps(rh, dh) + ry
+    luma = _row_sectors(ys * int(pitch), xs)
+    cx = np.unique(xs // 2)
+    ccols = (2 * cx[:, None] + np.arange(2)[None, :]).ravel()
+    chroma = _row_sectors((height + np.unique(ys // 2)) * int(pitch), ccols)
+    return SECTOR * (luma + chroma)
+
+
+def planar_out_sector_bytes(n, h, w, bytes_per_el, channels=3) -> int:
+    """Sectors written by dense [n, C, h, w] planes (32-byte aligned base)."""
+    row = w * bytes_per_el
+    starts = np.arange(n * channels * h, dtype=np.int64) * row
+    first, last = starts // SECTOR, (starts + row - 1) // SECTOR
+    # rows may share a sector at their boundary: count distinct sectors
+    return SECTOR * int(len(np.unique(np.concatenate([np.arange(a, b + 1) for a, b in zip(first, last)])))
+                        if row % SECTOR else np.sum(last - first + 1))
+
+
 # ------------------------------------------------------------------ clocks
 
 

@@ -43,12 +43,11 @@ def source_hash(files: list[str] | None = None) -> str:
     return h.hexdigest()[:16]
 
 
-# Every header the fused image-chain kernels are compiled with (registry.h
-# fixes the parameter-table capacity, a template argument of the kernels). A
-# traffic entry hashes these plus its translation unit; host-only sources
-# (api.cu, the other families) are not part of it.
-DEVICE_HEADERS = ["fkl/core.cuh", "fkl/ops.cuh", "fkl/dpp.cuh", "fkl/staged.cuh", "float_family.cuh",
-                  "registry.h"]
+# Every header the device code of the fused image-chain kernels comes from
+# (core.cuh also fixes the parameter-table capacity, a template argument of
+# the kernels). A traffic entry hashes these plus its translation unit;
+# host-only sources (registry.h, api.cu, the other families) are not part of it.
+DEVICE_HEADERS = ["fkl/core.cuh", "fkl/ops.cuh", "fkl/dpp.cuh", "fkl/staged.cuh", "float_family.cuh"]
 
 
 def entry_hash(entry: dict) -> str:

@@ -1,0 +1,31 @@
+"""Host-side pieces of bench.py that run without a GPU."""
+import os
+import sys
+import types
+
+import pytest
+
+sys.path.insert(0, os.path.dirname(os.path.dirname(os.path.abspath(__file__))))
+import bench  # noqa: E402
+
+
+@pytest.mark.parametrize("kind,params", [("single", {}), ("vchain", {"L": 10})])
+def test_parallel_oracle_baseline_runs_in_spawned_workers(kind, params):
+    wl = types.SimpleNamespace(oracle_spec=(kind, params, 1000.0))
+    args = types.SimpleNamespace(cpu_seconds=0.2)
+    r = bench.cpu_baseline_parallel(wl, args)
+    cores = len(os.sched_getaffinity(0)) if hasattr(os, "sched_getaffinity") else os.cpu_count()
+    assert r["cores"] == cores and r["kind"] == "oracle" and r["value"] > 0
+    assert "spawned worker processes" in r["sample"]
+
+
+def test_sector_footprints():
+    from paper_2508_07071_gb300 import metrics as M
+    # a 2x downscale of 64 columns touches every byte of 192 contiguous bytes: 6 sectors per row
+    assert M.packed_tap_sector_bytes(0, 0, 64, 2, 32, 1, 4096) == 2 * 6 * 32
+    # a 4x downscale reads the middle pair of every 4 columns: 2 of 4 pixels, yet every sector
+    assert M.packed_tap_bytes(64, 1, 16, 1) == 32 * 3 and M.packed_tap_sector_bytes(0, 0, 64, 1, 16, 1, 4096) == 6 * 32
+    # NV12 exact 2x of aligned rows: sectors equal bytes
+    assert M.nv12_tap_sector_bytes(0, 0, 1280, 720, 640, 360, 1280, 720) == M.nv12_tap_bytes(0, 0, 1280, 720, 640, 360)
+    # planes of 12-byte rows share sectors across rows: counted once
+    assert M.planar_out_sector_bytes(1, 8, 3, 4) == 3 * 8 * 12
