@@ -460,8 +460,11 @@ std::vector<fkl_launch_shape> shapes_for(const Spec& s) {
   if (s.family == FAM_INT) {
     vecs = {16};
   } else if (s.family == FAM_PACKED || s.family == FAM_NV12) {
+    const bool packed = s.family == FAM_PACKED;  // the packed reader also runs 1-2 pixels per thread
     if (s.out_dtype == FKL_F32)
-      vecs = s.split ? std::vector<int>{4, 8} : std::vector<int>{4};
+      vecs = !s.split ? std::vector<int>{4} : packed ? std::vector<int>{1, 2, 4, 8} : std::vector<int>{4, 8};
+    else if (packed && (s.out_dtype == FKL_F16 || s.out_dtype == FKL_BF16))
+      vecs = {2, 8, 16};
     else
       vecs = {8, 16};
   } else {

@@ -38,6 +38,24 @@ struct VecSet<fkl::e4m3_t, true> {
   static constexpr int v[] = {8, 16};
 };
 
+// The packed-u8 reader also takes 1 and 2 pixels per thread: its workloads
+// (one image, crops) are small, and more threads in flight hide their
+// latency. (The NV12 exact-2x path reads 16-byte vectors: 8 pixels or more.)
+template <class ROp, class OutT, bool kSplit>
+struct VecSetFor : VecSet<OutT, kSplit> {};
+template <>
+struct VecSetFor<fkl::ResizeU8C3, float, true> {
+  static constexpr int v[] = {1, 2, 4, 8};
+};
+template <>
+struct VecSetFor<fkl::ResizeU8C3, fkl::f16_t, true> {
+  static constexpr int v[] = {2, 8, 16};
+};
+template <>
+struct VecSetFor<fkl::ResizeU8C3, fkl::bf16_t, true> {
+  static constexpr int v[] = {2, 8, 16};
+};
+
 // Compute ops after the optional swap, fixed at compile time so that an
 // absent op costs nothing: 0 = Mul; 1 = Mul, Sub; 2 = Mul, Sub, Div.
 // (An absent Mul or Sub inside a tail is bound as its exact identity.)
@@ -214,8 +232,9 @@ cudaError_t float_by_ry(const LaunchCtx& c) {
 template <class ROp, class OutT, bool kSplit, bool kSwap, int kTail, size_t... I>
 cudaError_t float_by_vec(const LaunchCtx& c, std::index_sequence<I...>) {
   cudaError_t err = cudaErrorInvalidConfiguration;
-  const bool hit = ((c.shape.vec == VecSet<OutT, kSplit>::v[I]
-                         ? (err = float_by_ry<ROp, OutT, kSplit, kSwap, kTail, VecSet<OutT, kSplit>::v[I]>(c), true)
+  const bool hit = ((c.shape.vec == VecSetFor<ROp, OutT, kSplit>::v[I]
+                         ? (err = float_by_ry<ROp, OutT, kSplit, kSwap, kTail, VecSetFor<ROp, OutT, kSplit>::v[I]>(c),
+                            true)
                          : false) ||
                     ...);
   (void)hit;
@@ -224,7 +243,7 @@ cudaError_t float_by_vec(const LaunchCtx& c, std::index_sequence<I...>) {
 
 template <class ROp, class OutT, bool kSplit, bool kSwap>
 cudaError_t float_by_type(const LaunchCtx& c) {
-  constexpr size_t n = sizeof(VecSet<OutT, kSplit>::v) / sizeof(int);
+  constexpr size_t n = sizeof(VecSetFor<ROp, OutT, kSplit>::v) / sizeof(int);
   switch (tail_of(*c.spec)) {
     case 0:
       return float_by_vec<ROp, OutT, kSplit, kSwap, 0>(c, std::make_index_sequence<n>{});
