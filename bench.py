@@ -126,10 +126,15 @@ class NV12Letterbox(Workload):
         self.host_o = F.as_fkl(self.host_out, F.FKL_LAYOUT_NCHW)
         self.executor = F.fkl_host_executor_create(self.pipe.handle, chunk, depth, self.h * 3 // 2 * self.w,
                                                    3 * self.out * self.out * self.el)
-        self.e2e_launches = (self.n + chunk - 1) // chunk
-        self.e2e_note = f"fkl_execute_batch_host, chunks of {chunk} frames, {depth} device slots"
+        self.e2e_launches = self.launches_per_step
+        self.e2e_note = ("fkl_execute_batch_mapped: the fused kernel reads the pinned host frames and writes "
+                         "the pinned host planes over the host link (no staging copies)")
+        self.e2e_staged_note = f"fkl_execute_batch_host, chunks of {chunk} frames, {depth} device slots"
 
     def e2e_step(self, stream):
+        self.F.fkl_execute_batch_mapped(self.pipe.handle, self.host_ins, None, self.host_o, stream=stream)
+
+    def e2e_staged_step(self, stream):
         self.F.fkl_execute_batch_host(self.executor, self.host_ins, None, self.host_o, stream=stream)
 
     def link_copy(self, stream):
@@ -391,13 +396,20 @@ def run_ours(args):
         # end to end through the public call with host buffers
         ke = min(args.steps, args.e2e_steps)
         e2e_ms = link_ms = None
+        e2e_paths = {}
         if ke > 0:
             wl.e2e_setup()
-            for _ in range(2):
-                wl.e2e_step(stream)
-            torch.cuda.synchronize()
-            e2e_ms = float(np.mean(time_steps(torch, wl.e2e_step, ke, stream)))
-            link_ms = None
+            # each public host-buffer call the workload offers, staged copies first
+            calls = [(getattr(wl, "e2e_staged_note", None), getattr(wl, "e2e_staged_step", None)),
+                     (getattr(wl, "e2e_note", "torch pinned copies + fkl_execute_batch on one stream"), wl.e2e_step)]
+            for note, fn in calls:
+                if fn is None:
+                    continue
+                for _ in range(2):
+                    fn(stream)
+                torch.cuda.synchronize()
+                e2e_paths[note] = float(np.mean(time_steps(torch, fn, ke, stream)))
+            e2e_note, e2e_ms = min(e2e_paths.items(), key=lambda kv: kv[1])
             if hasattr(wl, "link_copy"):
                 wl.link_copy(stream)
                 link_ms = float(np.mean(time_steps(torch, wl.link_copy, ke, stream)))
@@ -456,9 +468,10 @@ def run_ours(args):
             "value": round(wl.bytes * world / (e2e_ms * 1e-3) / 1e9, 1), "unit": "GB/s",
             "ms_per_step": round(e2e_ms, 4), "h2d_bytes_per_step": int(wl.h2d_bytes),
             "d2h_bytes_per_step": int(wl.d2h_bytes), "steps": ke,
-            "path": getattr(wl, "e2e_note", "torch pinned copies + fkl_execute_batch on one stream"),
+            "path": e2e_note,
             "link_copy_ms": None if link_ms is None else round(link_ms, 4),
-            "frac_of_link": None if link_ms is None else round(link_ms / e2e_ms, 3)},
+            "frac_of_link": None if link_ms is None else round(link_ms / e2e_ms, 3),
+            "ms_per_step_by_path": {k: round(v, 4) for k, v in e2e_paths.items()}},
         "gpu_launches": int(args.steps * wl.launches_per_step),
         "clocks": clocks,
         "wall_s_timed": round(wall, 4),

@@ -297,6 +297,21 @@ FKL_API fkl_status fkl_execute_batch_scaled(fkl_pipeline p, int32_t n, const fkl
                                             const int32_t* rois, fkl_tensor* out, const float* scale_inv_dev,
                                             void* stream);
 
+/*
+ * fkl_execute_batch on buffers in pinned host memory (cudaHostAlloc, or
+ * cudaHostRegister'ed), read and written by the fused kernel itself over the
+ * host link (no staging copies: on a Grace host the NVLink-C2C link is
+ * coherent, and the one kernel streams the inputs in and the outputs out).
+ * Every input and the output may each be pinned host memory or device memory;
+ * each pointer is checked with cudaPointerGetAttributes and replaced by its
+ * device address. Pageable (unregistered) host memory is FKL_ERR_INVALID and
+ * nothing is launched. Arguments and results are otherwise those of
+ * fkl_execute_batch; the host buffers must stay valid until `stream` has
+ * passed the launch.
+ */
+FKL_API fkl_status fkl_execute_batch_mapped(fkl_pipeline p, int32_t n, const fkl_tensor* ins,
+                                            const int32_t* rois, fkl_tensor* out, void* stream);
+
 /* ------------------------------------------------------------------------ */
 /* Host-buffer executor: overlapped copy-in, fused launch, copy-out          */
 /* ------------------------------------------------------------------------ */

@@ -746,6 +746,45 @@ fkl_status fkl_execute_batch(fkl_pipeline p, int32_t n, const fkl_tensor* ins, c
 }
 
 
+fkl_status fkl_execute_batch_mapped(fkl_pipeline p, int32_t n, const fkl_tensor* ins, const int32_t* rois,
+                                    fkl_tensor* out, void* stream) {
+  if (!p) return fail(FKL_ERR_INVALID, "null pipeline");
+  if (n < 0 || (n > 0 && !ins) || !out) return fail(FKL_ERR_INVALID, "bad batch arguments");
+  // the device address of a pinned host or device buffer; pageable memory is refused
+  auto device_address = [](void* ptr, void** dev, const char* what, int i) -> fkl_status {
+    if (!ptr) {
+      *dev = nullptr;
+      return FKL_OK;
+    }
+    cudaPointerAttributes a;
+    const cudaError_t e = cudaPointerGetAttributes(&a, ptr);
+    if (e != cudaSuccess) return cuda_fail(e, "pointer attributes");
+    if (a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged) {
+      *dev = ptr;
+      return FKL_OK;
+    }
+    if (a.type == cudaMemoryTypeHost && a.devicePointer) {
+      *dev = a.devicePointer;
+      return FKL_OK;
+    }
+    return fail(FKL_ERR_INVALID, "%s %d: not pinned host memory or device memory", what, i);
+  };
+  std::vector<fkl_tensor> dins;
+  try {
+    dins.assign(ins, ins + n);
+  } catch (...) {
+    return fail(FKL_ERR_OOM, "host allocation failed");
+  }
+  for (int i = 0; i < n; ++i) {
+    const fkl_status st = device_address(ins[i].data, &dins[i].data, "input", i);
+    if (st != FKL_OK) return st;
+  }
+  fkl_tensor dout = *out;
+  const fkl_status st = device_address(out->data, &dout.data, "output", 0);
+  if (st != FKL_OK) return st;
+  return fkl_execute_batch(p, n, dins.data(), rois, &dout, stream);
+}
+
 fkl_status fkl_execute_batch_scaled(fkl_pipeline p, int32_t n, const fkl_tensor* ins, const int32_t* rois,
                                     fkl_tensor* out, const float* scale_inv_dev, void* stream) {
   if (!p) return fail(FKL_ERR_INVALID, "null pipeline");

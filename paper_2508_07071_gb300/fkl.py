@@ -156,6 +156,9 @@ EXPORTS = {
                                                 ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(fkl_tensor),
                                                 ctypes.c_void_p, ctypes.c_void_p]),
     "fkl_device_check": (ctypes.c_int, []),
+    "fkl_execute_batch_mapped": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int32, ctypes.POINTER(fkl_tensor),
+                                                ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(fkl_tensor),
+                                                ctypes.c_void_p]),
     "fkl_set_device_wait_limit": (ctypes.c_int, [ctypes.c_uint64]),
     "fkl_version": (ctypes.c_char_p, []),
 }
@@ -435,6 +438,15 @@ def fkl_execute_batch(p: int, ins: Sequence[fkl_tensor], rois, out: fkl_tensor, 
     keep = _rois(rois)
     _check(_lib.fkl_execute_batch(p, len(ins), arr, keep[1] if keep else None, ctypes.byref(out),
                                   _stream(stream)))
+
+
+def fkl_execute_batch_mapped(p: int, ins: Sequence[fkl_tensor], rois, out: fkl_tensor, stream=None) -> None:
+    """fkl_execute_batch on pinned host (or device) buffers, read and written
+    by the fused kernel over the host link."""
+    arr = (fkl_tensor * max(1, len(ins)))(*ins)
+    keep = _rois(rois)
+    _check(_lib.fkl_execute_batch_mapped(p, len(ins), arr, keep[1] if keep else None, ctypes.byref(out),
+                                         _stream(stream)))
 
 
 FKL_REDUCE_STATS_BYTES = 128

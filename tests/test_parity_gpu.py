@@ -784,3 +784,47 @@ def test_device_cast_exhaustive_over_0_to_448(F, W, dst):
         got = _decode(F, o, dst)
         bad = np.nonzero(got != want)[0]
         assert bad.size == 0, (dst, hex(start + int(bad[0])), got[bad[0]], want[bad[0]])
+
+
+# ------------------------------------------------------------------ pinned host buffers read and written by the kernel
+
+def test_mapped_host_buffers_match_device_path(F, W):
+    frames = synth.nv12_frames(15, 6, 720, 1280)
+    ops = W.nv12_letterbox_chain(F.FKL_BF16)
+    p = F.Pipeline(ops)
+    dev_in = torch.from_numpy(frames).cuda()
+    base = torch.empty((6, 3, 640, 640), dtype=torch.bfloat16, device="cuda")
+    F.fkl_execute_batch(p.handle, [F.as_fkl(dev_in[i], F.FKL_LAYOUT_NV12) for i in range(6)], None,
+                        F.as_fkl(base, F.FKL_LAYOUT_NCHW))
+    host_in = torch.from_numpy(frames).pin_memory()
+    host_out = torch.zeros((6, 3, 640, 640), dtype=torch.bfloat16).pin_memory()
+    ins_h = [F.as_fkl(host_in[i], F.FKL_LAYOUT_NV12) for i in range(6)]
+    F.fkl_execute_batch_mapped(p.handle, ins_h, None, F.as_fkl(host_out, F.FKL_LAYOUT_NCHW))
+    torch.cuda.synchronize()
+    assert torch.equal(host_out.view(torch.int16), base.cpu().view(torch.int16))
+    # mixed: host inputs, device output
+    dev_out = torch.zeros_like(base)
+    F.fkl_execute_batch_mapped(p.handle, ins_h, None, F.as_fkl(dev_out, F.FKL_LAYOUT_NCHW))
+    torch.cuda.synchronize()
+    assert torch.equal(dev_out.view(torch.int16), base.view(torch.int16))
+    want = O.preprocess_nv12(frames[5], 640, 640, pad=114.0, mul=1 / 255)
+    check_output(host_out[5], want, "bf16", 1.0, "mapped frame 5")
+
+
+def test_mapped_typed_chain_and_pageable_memory_is_refused(F, W):
+    xs = [synth.linear_values(31 + i, 5000, "u16") for i in range(4)]
+    ops = W.typed_chain(F.FKL_U16, F.FKL_F32, 1 / 255, 0.5, 0.25)
+    p = F.Pipeline(ops)
+    want = np.concatenate([O.typed_chain(x, "f32", 1 / 255, 0.5, 0.25) for x in xs])
+    host = [torch.from_numpy(x).pin_memory() for x in xs]
+    out = torch.full((4 * 5000,), float("nan")).pin_memory()
+    F.fkl_execute_batch_mapped(p.handle, [F.as_fkl(h) for h in host], None, F.as_fkl(out))
+    torch.cuda.synchronize()
+    assert _bits_equal(out.numpy(), want)
+    pageable = torch.from_numpy(xs[0].copy())          # ordinary host memory: never handed to a kernel
+    out2 = torch.full((5000,), -1.0).pin_memory()
+    with pytest.raises(F.FklError) as e:
+        F.fkl_execute_batch_mapped(p.handle, [F.as_fkl(pageable)], None, F.as_fkl(out2))
+    assert e.value.status == F.FKL_ERR_INVALID
+    torch.cuda.synchronize()
+    assert float(out2[0]) == -1.0
