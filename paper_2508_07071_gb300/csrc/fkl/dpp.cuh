@@ -21,17 +21,27 @@ struct Args2D {
   int32_t H, W_;  // output rows and columns per image
 };
 
-// One body, two kernels. The exact-2x NV12 read writing FP8 with 16 pixels
-// per thread (78 registers when unbounded, 6 blocks of 128 threads per SM) is
-// compiled for at least 4 blocks of 256 threads per SM (64 registers, 16-44
-// spilled bytes): the extra occupancy lifted that chain by 5%. Every other
-// variant keeps the compiler's register choice; under the same cap the
-// 16-bit outputs, the general resize and the two-row variants spilled
-// 44-550 bytes, and the 8-pixel ones already use <= 64 registers.
+// One body, two kernels. Most variants keep the compiler's register choice;
+// the exact-2x NV12 read writing 16-bit or FP8 planes is compiled for a
+// minimum number of resident 256-thread blocks per SM (OccupancyBound), which
+// caps its registers: 8 pixels per thread, bf16/f16, 6 blocks (40 registers
+// instead of 48, 16 spilled bytes; +2% on 256 frames); 16 pixels per thread,
+// FP8, 4 blocks (64 instead of 78, 16-44 spilled bytes; +5%). These loads are
+// latency-bound, so more resident warps pay for the spills; under the same
+// caps the general resize and the two-row variants spilled 44-550 bytes.
 template <class RB, class W, int V, int RY>
-struct OccupancyBound : std::false_type {};
+struct OccupancyBase : std::integral_constant<int, 0> {};  // 0: the compiler's choice
 template <int CAP>
-struct OccupancyBound<BatchRead<ResizeNV12x2, CAP>, WriteSplit<e4m3_t, 3>, 16, 1> : std::true_type {};
+struct OccupancyBase<BatchRead<ResizeNV12x2, CAP>, WriteSplit<e4m3_t, 3>, 16, 1> : std::integral_constant<int, 4> {};
+template <int CAP>
+struct OccupancyBase<BatchRead<ResizeNV12x2, CAP>, WriteSplit<bf16_t, 3>, 8, 1> : std::integral_constant<int, 6> {};
+template <int CAP>
+struct OccupancyBase<BatchRead<ResizeNV12x2, CAP>, WriteSplit<f16_t, 3>, 8, 1> : std::integral_constant<int, 6> {};
+// Only chains that run on packed pixel pairs (a chain that divides does not,
+// and spilled 44-80 bytes under the cap).
+template <class RB, class W, class Cops, int V, int RY>
+struct OccupancyBound
+    : std::integral_constant<int, ChainHasPair<Cops>::value ? OccupancyBase<RB, W, V, RY>::value : 0> {};
 
 template <int V, int RY, class RB, class W, class Cops>
 FKL_D void transform2d_body(const Args2D<RB, W, Cops>& a) {
@@ -84,8 +94,8 @@ template <int V, int RY, class RB, class W, class Cops>
 __global__ void __launch_bounds__(256) transform2d_kernel(const __grid_constant__ Args2D<RB, W, Cops> a) {
   transform2d_body<V, RY>(a);
 }
-template <int V, int RY, class RB, class W, class Cops>
-__global__ void __launch_bounds__(256, 4) transform2d_occ_kernel(const __grid_constant__ Args2D<RB, W, Cops> a) {
+template <int V, int RY, int kMinBlocks, class RB, class W, class Cops>
+__global__ void __launch_bounds__(256, kMinBlocks) transform2d_occ_kernel(const __grid_constant__ Args2D<RB, W, Cops> a) {
   transform2d_body<V, RY>(a);
 }
 
@@ -99,8 +109,9 @@ cudaError_t launch_transform2d(Args2D<RB, W, Cops>& a, int batch, int tx, int ty
   const int rows = (a.H + RY - 1) / RY;
   const dim3 block(tx, ty, 1);
   const dim3 grid((cols + tx - 1) / tx, (rows + ty - 1) / ty, batch);
-  if constexpr (OccupancyBound<RB, W, V, RY>::value) {
-    transform2d_occ_kernel<V, RY, RB, W, Cops><<<grid, block, 0, s>>>(a);
+  constexpr int kMinBlocks = OccupancyBound<RB, W, Cops, V, RY>::value;
+  if constexpr (kMinBlocks > 0) {
+    transform2d_occ_kernel<V, RY, kMinBlocks, RB, W, Cops><<<grid, block, 0, s>>>(a);
   } else {
     transform2d_kernel<V, RY, RB, W, Cops><<<grid, block, 0, s>>>(a);
   }
