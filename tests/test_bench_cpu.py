@@ -29,3 +29,19 @@ def test_sector_footprints():
     assert M.nv12_tap_sector_bytes(0, 0, 1280, 720, 640, 360, 1280, 720) == M.nv12_tap_bytes(0, 0, 1280, 720, 640, 360)
     # planes of 12-byte rows share sectors across rows: counted once
     assert M.planar_out_sector_bytes(1, 8, 3, 4) == 3 * 8 * 12
+
+
+def test_reference_arm_prints_the_contract_line():
+    import json
+    import subprocess
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    r = subprocess.run([sys.executable, "bench.py", "--impl", "reference", "--steps", "2", "--warmup", "3"],
+                       cwd=root, capture_output=True, text=True, timeout=600)
+    assert r.returncode == 0, r.stderr[-2000:]
+    line = json.loads([l for l in r.stdout.splitlines() if l.startswith("{")][-1])
+    for key in ("metric", "value", "unit", "n_gpus", "steps", "warmup", "ms_per_step", "higher_is_better",
+                "scaling", "vs_baseline", "dtype", "data", "config", "cpu_baseline", "e2e"):
+        assert key in line, key
+    assert line["impl"] == "reference" and line["value"] > 0 and line["unit"] == "GB/s"
+    assert line["cpu_baseline"]["kind"] == "oracle" and line["cpu_baseline"]["cores"] >= 1
+    assert line["e2e"]["h2d_bytes_per_step"] == 0 and line["e2e"]["value"] == line["value"]
