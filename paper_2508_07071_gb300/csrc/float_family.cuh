@@ -85,6 +85,7 @@ auto make_tail(const Spec& s) {
 // carries its whole parameter block, 16 KB for kBatchCap entries), for ROps
 // that serve single images.
 constexpr int kSmallCap = 8;
+constexpr int kMidCap = 64;  // 4 KB of parameters: crop batches of tens of images
 template <class ROp>
 struct SmallBatches : std::false_type {};
 template <>
@@ -119,6 +120,7 @@ template <class ROp, class OutT, bool kSplit, bool kSwap, int kTail, int V, int 
 cudaError_t run_float_chain(const LaunchCtx& c) {
   if constexpr (SmallBatches<ROp>::value) {
     if (c.n <= kSmallCap) return run_float_chain_cap<ROp, OutT, kSplit, kSwap, kTail, V, RY, kSmallCap>(c);
+    if (c.n <= kMidCap) return run_float_chain_cap<ROp, OutT, kSplit, kSwap, kTail, V, RY, kMidCap>(c);
   }
   return run_float_chain_cap<ROp, OutT, kSplit, kSwap, kTail, V, RY, kBatchCap>(c);
 }
