@@ -99,10 +99,6 @@ __global__ void __launch_bounds__(256, kMinBlocks) transform2d_occ_kernel(const 
   transform2d_body<V, RY>(a);
 }
 
-struct Shape2D {
-  int vec, tx, ty, ry;
-};
-
 template <int V, int RY, class RB, class W, class Cops>
 cudaError_t launch_transform2d(Args2D<RB, W, Cops>& a, int batch, int tx, int ty, cudaStream_t s) {
   const int cols = (a.W_ + V - 1) / V;
