@@ -86,7 +86,7 @@ bool is_compute(int op) {
          op == FKL_OP_DIV || op == FKL_OP_ADD_SAT_U8;
 }
 
-// Typed chains: READ_{U8,U16,F32,F64} [MUL] [ADD|SUB] [DIV] WRITE_PACKED(F32|F64).
+// Typed chains: READ_{U8,U16,F32,F64} [MUL] [ADD|SUB] [DIV] WRITE_PACKED(F32|F64|F16|BF16|E4M3).
 fkl_status parse_typed(const fkl_op_desc* ops, int n, int src, Spec& s) {
   s.family = FAM_CAST;
   s.in_dtype = src == FKL_OP_READ_U8 ? FKL_U8 : src == FKL_OP_READ_U16 ? FKL_U16
@@ -745,7 +745,6 @@ fkl_status fkl_execute_batch(fkl_pipeline p, int32_t n, const fkl_tensor* ins, c
   return execute_batch_impl(p, n, ins, rois, out, nullptr, stream);
 }
 
-
 fkl_status fkl_execute_batch_mapped(fkl_pipeline p, int32_t n, const fkl_tensor* ins, const int32_t* rois,
                                     fkl_tensor* out, void* stream) {
   if (!p) return fail(FKL_ERR_INVALID, "null pipeline");
@@ -916,10 +915,7 @@ fkl_status fkl_pipeline_autotune_ex(fkl_pipeline p, int32_t n, const fkl_tensor*
   constexpr int kMaxReps = 32;
   if (!p) return fail(FKL_ERR_INVALID, "null pipeline");
   if (reps < 1 || reps > kMaxReps) return fail(FKL_ERR_INVALID, "reps must be in 1..%d", kMaxReps);
-  const bool vchain = p->spec.family == FAM_VCHAIN;
-  auto run = [&]() -> fkl_status {
-    return vchain ? fkl_execute(p, ins, out, stream) : fkl_execute_batch(p, n, ins, rois, out, stream);
-  };
+  auto run = [&]() -> fkl_status { return fkl_execute_batch(p, n, ins, rois, out, stream); };
   const std::vector<fkl_launch_shape> shapes = shapes_for(p->spec);
   const fkl_launch_shape saved = p->shape;
   float best_t = -1.f;
@@ -979,9 +975,15 @@ fkl_status fkl_execute_batch_unfused_static(fkl_pipeline p, int32_t n, const fkl
   if (!p) return fail(FKL_ERR_INVALID, "null pipeline");
   const cudaStream_t s = static_cast<cudaStream_t>(stream);
   if (is_tensor_chain(p->spec)) {  // the float32 copy of one tensor, if any, lives in the static scratch
+    int64_t len = 0;
+    std::vector<const void*> ptrs;
+    const fkl_status st = check_linear(p->spec, n, ins, rois, out, len, ptrs);
+    if (st != FKL_OK) return st;
     void* scratch = nullptr;
-    const cudaError_t e = static_scratch(&scratch);
-    if (e != cudaSuccess) return cuda_fail(e, "static scratch lookup");
+    if (linear_workspace_bytes(p->spec, len) > 0) {
+      const cudaError_t e = static_scratch(&scratch);
+      if (e != cudaSuccess) return cuda_fail(e, "static scratch lookup");
+    }
     return run_linear(p, n, ins, rois, out, true, stream, scratch, kStaticScratchBytes);
   }
   if (n < 0) return fail(FKL_ERR_INVALID, "negative batch size");

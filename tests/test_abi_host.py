@@ -278,3 +278,16 @@ def test_typed_chain_narrow_outputs_parse(F):
         assert ei.value.status == F.FKL_ERR_INVALID
     finally:
         F.fkl_pipeline_destroy(p)
+
+
+def test_static_unfused_validates_tensor_chains_before_any_device_call(F):
+    from paper_2508_07071_gb300 import workloads as W
+    p = F.fkl_pipeline_create(W.typed_chain(F.FKL_F64, F.FKL_BF16, 2.0))
+    try:
+        a = F._tensor(0x1000, (1000,), 0, F.FKL_F64, F.FKL_LAYOUT_LINEAR)
+        short = F._tensor(0x9000, (1999,), 0, F.FKL_BF16, F.FKL_LAYOUT_LINEAR)
+        with pytest.raises(F.FklError) as ei:
+            F.fkl_execute_batch_unfused_static(p, [a, a], None, short, stream=0)
+        assert ei.value.status == F.FKL_ERR_INVALID
+    finally:
+        F.fkl_pipeline_destroy(p)
