@@ -21,7 +21,10 @@
  * kernel implements is FKL_ERR_UNSUPPORTED.
  *
  * Thread safety: distinct pipelines may be used from distinct threads; one
- * pipeline may be executed concurrently (it holds no per-call state).
+ * pipeline may be executed concurrently (it holds no per-call state), but
+ * fkl_pipeline_set_shape and fkl_pipeline_autotune change its launch shape
+ * and must not overlap other calls on the same pipeline.
+ * fkl_set_device_wait_limit is process-wide.
  */
 #ifndef FKL_H_
 #define FKL_H_
