@@ -828,3 +828,45 @@ def test_mapped_typed_chain_and_pageable_memory_is_refused(F, W):
     assert e.value.status == F.FKL_ERR_INVALID
     torch.cuda.synchronize()
     assert float(out2[0]) == -1.0
+
+
+def test_dynamic_fp8_scale_is_the_same_on_every_launch_shape(F, W):
+    """fkl_execute_batch_scaled reads the device-side 1/s in every kernel form
+    (register kernels, the row-staged kernel): identical codes."""
+    frames = synth.nv12_frames(18, 3, 720, 1280)
+    dev = torch.from_numpy(frames).cuda()
+    ins = [F.as_fkl(dev[i], F.FKL_LAYOUT_NV12) for i in range(3)]
+    p = F.Pipeline(W.nv12_letterbox_chain(F.FKL_E4M3, scale=1.0))
+    stats = torch.zeros(32, device="cuda")
+    probe = torch.zeros((3, 3, 640, 640), dtype=torch.float8_e4m3fn, device="cuda")
+    F.fkl_reduce_batch(p.handle, ins, None, F.as_fkl(probe, F.FKL_LAYOUT_NCHW), stats.data_ptr())
+    outs = []
+    for shape in [(8, 16, 8, 1), (16, 8, 16, 1), (8, 16, 8, 2), (16, 128, 4, -2), (8, 128, 2, -2)]:
+        F.fkl_pipeline_set_shape(p.handle, shape)
+        out = torch.zeros_like(probe)
+        F.fkl_execute_batch_scaled(p.handle, ins, None, F.as_fkl(out, F.FKL_LAYOUT_NCHW), stats.data_ptr() + 11 * 4)
+        outs.append(out)
+    torch.cuda.synchronize()
+    F.fkl_device_check()
+    for o in outs[1:]:
+        assert torch.equal(o.view(torch.uint8), outs[0].view(torch.uint8))
+    assert outs[0].view(torch.uint8).max().item() == 0x7E
+
+
+def test_typed_chain_replays_in_a_cuda_graph(F, W):
+    xs = [torch.from_numpy(synth.linear_values(90 + i, 4096, "f64")).cuda() for i in range(8)]
+    p = F.Pipeline(W.typed_chain(F.FKL_F64, F.FKL_BF16, 1 / 3, 0.25, 0.5))
+    ins = [F.as_fkl(x) for x in xs]
+    out = torch.zeros(8 * 4096, dtype=torch.bfloat16, device="cuda")
+    s = torch.cuda.Stream()
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.stream(s):
+        F.fkl_execute_batch(p.handle, ins, None, F.as_fkl(out), stream=s)  # warm
+        torch.cuda.synchronize()
+        out.zero_()
+        with torch.cuda.graph(g, stream=s):
+            F.fkl_execute_batch(p.handle, ins, None, F.as_fkl(out), stream=s)
+    g.replay()
+    torch.cuda.synchronize()
+    want = np.concatenate([O.typed_chain(x.cpu().numpy(), "bf16", 1 / 3, 0.25, 0.5) for x in xs])
+    assert np.array_equal(_decode(F, out, "bf16"), want)
