@@ -649,9 +649,11 @@ def run_sweeps(args):
         return not only or name in only
 
     def t(fn, k):
+        # device time of k queued calls: the small sizes are launch-bound,
+        # and a call that waits for the host would time the host
         fn(stream)
         torch.cuda.synchronize()
-        return float(np.median(time_steps(torch, fn, k, stream)))
+        return float(np.median(time_steps_queued(torch, fn, k, stream)))
 
     with torch.cuda.stream(stream):
         # Exp 4: VF + HF, u8 input, batch 50 x 60 x 120 (one launch for the batch)

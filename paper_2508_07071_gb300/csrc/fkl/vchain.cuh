@@ -43,11 +43,13 @@ FKL_D void vchain_load(const void* in, int64_t base, int64_t n, bool vec, float 
       for (int e = 0; e < E; ++e) x[e] = base + e < n ? f[base + e] : 0.f;
     }
   } else {
-    static_assert(std::is_same_v<InT, uint8_t> && E % 8 == 0, "u8 chains load 8-byte multiples");
+    static_assert(std::is_same_v<InT, uint8_t> && (E == 4 || E % 8 == 0), "u8 chains load 4 or 8-byte multiples");
     const uint8_t* b = static_cast<const uint8_t*>(in);
     if (vec) {
       uint32_t w[E / 4];
-      if constexpr (E == 8) {
+      if constexpr (E == 4) {
+        w[0] = __ldcs(reinterpret_cast<const unsigned int*>(b + base));
+      } else if constexpr (E == 8) {
         const uint2 v = __ldcs(reinterpret_cast<const uint2*>(b + base));
         w[0] = v.x;
         w[1] = v.y;
@@ -84,12 +86,25 @@ __global__ void __launch_bounds__(512) vchain_kernel(const __grid_constant__ VCh
     if constexpr (kAlt) {
       // Mul, Add pairs: no per-op branch; each pair's two constants come in
       // one 8-byte load, and four pairs per loop trip amortise the loop.
+      // The Mul runs on two elements per packed f32x2 multiply and the Add
+      // on scalar adds: three FP32 issue slots per two elements and pair
+      // instead of four, for the same FP32 lane work, so the constant loads
+      // and the loop fit beside the FP32 pipe. (A packed multiply feeding a
+      // packed add is contracted into a multiply-add by the assembler, which
+      // rounds once where the chain rounds twice; with either side scalar it
+      // is not.)
       int i = 0;
 #pragma unroll 4
       for (; i + 1 < p.len; i += 2) {
         const float2 cc = *reinterpret_cast<const float2*>(&p.c[i]);  // i is even: 8-byte aligned
+        const F2 cm = f2s(cc.x);
 #pragma unroll
-        for (int e = 0; e < E; ++e) x[e] = __fadd_rn(__fmul_rn(x[e], cc.x), cc.y);
+        for (int e = 0; e < E; e += 2) {
+          float lo, hi;
+          f2split(f2mul(f2(x[e], x[e + 1]), cm), lo, hi);
+          x[e] = __fadd_rn(lo, cc.y);
+          x[e + 1] = __fadd_rn(hi, cc.y);
+        }
       }
       if (i < p.len) {
         const float cm = p.c[i];

@@ -54,6 +54,8 @@ cudaError_t run_shape(const Spec& s, const fkl_launch_shape& sh, size_t start, i
                       float* out, int64_t n, cudaStream_t st) {
   const bool persistent = sh.ry != 0;
   switch (sh.vec) {
+    case 4:
+      return run_chunk<1, CAP>(s, start, len, in, in_u8, out, n, sh.tx, persistent, st);
     case 8:
       return run_chunk<2, CAP>(s, start, len, in, in_u8, out, n, sh.tx, persistent, st);
     case 16:
