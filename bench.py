@@ -635,7 +635,9 @@ def run_sweeps(args):
     3840*2160*8 floats split into N kernels of M = 500/N ops each;
     Exp 6 (§VI-F) host time of one call; Exp 9 (§VI-I) data types: 50
     matrices of 60x120, Read -> Cast -> Mul -> Sub -> Div -> Write for every
-    (input, output) type pair. `--only exp4,exp9` runs a subset."""
+    (input, output) type pair; ReduceDPP (§IV-C) with dynamic FP8 scaling
+    on the 256-frame NV12 letterbox batch. `--only exp4,exp9` runs a
+    subset."""
     import torch
     import __graft_entry__
     __graft_entry__.build()
@@ -745,10 +747,10 @@ def run_sweeps(args):
                                              "speedup": round(unf / fused, 1)})
                 print(json.dumps({"exp6": res["exp6_cpu_time"][-1]}), flush=True)
         # Exp 9: data types, 50 x 60x120, Read -> Cast -> Mul -> Sub -> Div -> Write.
-        # "eager": one call per step from pre-marshalled arguments (what the
-        # host submits is part of the time, as in the paper's measurement);
-        # "graph": the same calls captured once in a CUDA graph and replayed
-        # (device time only).
+        # "eager": one call per step from pre-marshalled arguments, queued
+        # like every sweep call (device time of separately submitted
+        # launches); "graph": the same calls captured once in a CUDA graph
+        # and replayed.
         import ctypes
         cfg = W.DTYPES
         res["exp9_data_types"] = []
@@ -787,7 +789,51 @@ def run_sweeps(args):
                 row["shape"] = list(F.fkl_pipeline_get_shape(h))
                 res["exp9_data_types"].append(row)
                 print(json.dumps({"exp9": row}), flush=True)
-    print(json.dumps({"metric": "paper sweeps (Exp 4, 5, 6, 7, 9) on GB300", "results": res}), flush=True)
+        # ReduceDPP (§IV-C) and dynamic FP8 scaling on the 256-frame NV12
+        # letterbox batch: the reduction pass alone (it reads the frames and
+        # writes no image), the FP8 write with the scale that pass leaves in
+        # device memory, the two as one step, and the static-scale write.
+        if want("reduce"):
+            cfgn = W.NV12
+            n, h, w, side = cfgn["n"], cfgn["h"], cfgn["w"], cfgn["out"]
+            frames = torch.from_numpy(synth.nv12_frames(3, n, h, w)).cuda()
+            ins = [F.as_fkl(frames[i], F.FKL_LAYOUT_NV12) for i in range(n)]
+            p = F.Pipeline(W.nv12_letterbox_chain(F.FKL_E4M3, out=side, pad=cfgn["pad"]))
+            dst = torch.empty((n, 3, side, side), dtype=torch.float8_e4m3fn, device="cuda")
+            o = F.as_fkl(dst, F.FKL_LAYOUT_NCHW)
+            F.fkl_pipeline_autotune(p.handle, ins, None, o, stream=stream, reps=3)
+            stats = torch.zeros(32, dtype=torch.float32, device="cuda")
+            sp = stats.data_ptr()
+
+            def red(st):
+                F.fkl_reduce_batch(p.handle, ins, None, o, sp, stream=st)
+
+            def scaled(st):
+                F.fkl_execute_batch_scaled(p.handle, ins, None, o, sp + 11 * 4, stream=st)
+
+            def step(st):
+                red(st)
+                scaled(st)
+
+            def static(st):
+                F.fkl_execute_batch(p.handle, ins, None, o, stream=st)
+            read_b = n * h * w * 3 // 2
+            write_b = n * 3 * side * side
+            peak, peak_kind = measured_peaks()
+            ms = {name: t(fn, 20) for name, fn in (("reduce", red), ("scaled_write", scaled),
+                                                    ("dynamic_step", step), ("static_write", static))}
+            row = {k + "_us": round(1000 * v, 1) for k, v in ms.items()}
+            row["reduce_GBps"] = round(read_b / ms["reduce"] / 1e6, 1)
+            row["reduce_frac"] = round(read_b / ms["reduce"] / 1e6 / peak, 3)
+            row["dynamic_step_GBps"] = round((read_b + write_b) / ms["dynamic_step"] / 1e6, 1)
+            row["static_write_GBps"] = round((read_b + write_b) / ms["static_write"] / 1e6, 1)
+            row["peak_GBps"] = peak
+            row["peak"] = f"{peak_kind} copy bandwidth"
+            row["stats"] = [round(float(v), 6) for v in stats[:12].tolist()]
+            res["reduce_dynamic_fp8"] = row
+            print(json.dumps({"reduce": row}), flush=True)
+    print(json.dumps({"metric": "paper sweeps (Exp 4, 5, 6, 7, 9) and ReduceDPP on GB300", "results": res}),
+          flush=True)
 
 
 def run_reference(args):
@@ -853,7 +899,8 @@ def main():
     ap.add_argument("--no-autotune", action="store_true")
     ap.add_argument("--autotune-reps", type=int, default=7)
     ap.add_argument("--shape", default="", help="vec,tx,ty,ry launch shape (skips the autotuner)")
-    ap.add_argument("--only", default="", help="sweeps: comma-separated subset of exp4,exp5,exp6,exp7,exp9")
+    ap.add_argument("--only", default="",
+                    help="sweeps: comma-separated subset of exp4,exp5,exp6,exp7,exp9,reduce")
     args = ap.parse_args()
     if args.warmup < 3:
         raise SystemExit("--warmup must be >= 3")

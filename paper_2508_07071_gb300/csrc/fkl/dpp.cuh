@@ -43,6 +43,13 @@ template <class RB, class W, class Cops, int V, int RY>
 struct OccupancyBound
     : std::integral_constant<int, ChainHasPair<Cops>::value ? OccupancyBase<RB, W, V, RY>::value : 0> {};
 
+// A WOp may offer prepare(params): the parameters its threads write with,
+// computed once when a thread starts.
+template <class W, class = void>
+struct HasPrepare : std::false_type {};
+template <class W>
+struct HasPrepare<W, std::void_t<decltype(&W::prepare)>> : std::true_type {};
+
 template <int V, int RY, class RB, class W, class Cops>
 FKL_D void transform2d_body(const Args2D<RB, W, Cops>& a) {
   using RT = typename RB::OutputType;
@@ -54,6 +61,13 @@ FKL_D void transform2d_body(const Args2D<RB, W, Cops>& a) {
   const int z = blockIdx.z;
   if (x0 >= a.W_ || z >= a.rp.count) return;
   const int n = min(V, a.W_ - x0);
+  const typename W::ParamsType wp = [&] {
+    if constexpr (HasPrepare<W>::value) {
+      return W::prepare(a.wp);
+    } else {
+      return a.wp;
+    }
+  }();
 
   // Read every row first so that all loads of the thread are in flight
   // before the first store.
@@ -85,7 +99,7 @@ FKL_D void transform2d_body(const Args2D<RB, W, Cops>& a) {
 #pragma unroll
         for (int k = 0; k < V; ++k) out[k] = apply_chain(in[r][k], a.cops);
       }
-      W::template exec_span<V>(Point{x0, y, z}, n, out, a.wp);
+      W::template exec_span<V>(Point{x0, y, z}, n, out, wp);
     }
   }
 }

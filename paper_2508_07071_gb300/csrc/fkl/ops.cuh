@@ -303,20 +303,34 @@ struct ResizeNV12 {
   // multiply-add that would round differently from the scalar form.
   template <int V>
   static FKL_D void span_fast2x(const ParamsType& p, int lx, int ly, F3 (&out)[V]) {
+    uint4 a[V / 8], b[V / 8], c[V / 8];
+    load2x<V>(p, lx, ly, a, b, c);
+    compute2x<V>(a, b, c, out);
+  }
+
+  // Whether the V outputs from window position (lx, ly) take the 2x span
+  // path (exact 2x, inside the window, 16-byte aligned source).
+  template <int V>
+  static FKL_D bool fast2x(const ParamsType& p, int lx, int ly) {
+    return V % 8 == 0 && (p.flags & kFast2x) && ly >= 0 && ly < p.dh && lx >= 0 && lx + V <= p.dw &&
+           ((2 * lx) & 15) == 0;
+  }
+
+  // The 16-byte words of the 2x span: two luma rows and the chroma row.
+  template <int V>
+  static FKL_D void load2x(const ParamsType& p, int lx, int ly, uint4 (&a)[V / 8], uint4 (&b)[V / 8],
+                           uint4 (&c)[V / 8]) {
     static_assert(V % 8 == 0, "2x path reads 16-byte vectors");
-    constexpr int W = V / 8;  // uint4 per row
     const int64_t y0 = p.ry + 2 * ly;
     const uint4* r0 = reinterpret_cast<const uint4*>(p.src + y0 * p.pitch + p.rx + 2 * lx);
     const uint4* r1 = reinterpret_cast<const uint4*>(p.src + (y0 + 1) * p.pitch + p.rx + 2 * lx);
     const uint4* rc = reinterpret_cast<const uint4*>(p.uv + (y0 >> 1) * p.pitch + p.rx + 2 * lx);
-    uint4 a[W], b[W], c[W];
 #pragma unroll
-    for (int i = 0; i < W; ++i) {
+    for (int i = 0; i < V / 8; ++i) {
       a[i] = __ldg(r0 + i);
       b[i] = __ldg(r1 + i);
       c[i] = __ldg(rc + i);
     }
-    compute2x<V>(a, b, c, out);
   }
 
   // The arithmetic of the 2x span from the 16-byte words of the two luma
@@ -479,6 +493,7 @@ template <class ROp, int CAP>
 struct BatchRead {
   using InstanceType = ReadType;
   using OutputType = typename ROp::OutputType;
+  using Op = ROp;
   struct ParamsType {
     int32_t count;
     int32_t _pad[3];
@@ -650,6 +665,20 @@ struct WriteSplit {
     uint8_t* q = p.base + pt.z * p.img + pt.y * p.pitch + static_cast<int64_t>(pt.x) * B;
 #pragma unroll
     for (int c = 0; c < C; ++c) store_one<OutT>(q + c * p.plane, prescale<OutT>(v.v[c], p));
+  }
+
+  // The parameters a thread writes with: a dynamic FP8 scale is read from
+  // device memory once, when the thread starts, so that its latency overlaps
+  // the thread's source loads instead of stalling the write.
+  static FKL_D ParamsType prepare(const ParamsType& p) {
+    ParamsType q = p;
+    if constexpr (std::is_same_v<OutT, e4m3_t>) {
+      if (q.scale_inv_dev) {
+        q.scale_inv = __ldg(q.scale_inv_dev);
+        q.scale_inv_dev = nullptr;
+      }
+    }
+    return q;
   }
 
   // n <= V valid pixels starting at pt.x.

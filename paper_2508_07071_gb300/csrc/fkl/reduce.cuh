@@ -8,18 +8,19 @@ namespace fkl {
 // ReduceDPP (paper §IV-C, the reduction pattern): the ROp and COps of a chain
 // are evaluated once per output pixel, as in TransformDPP, and the values
 // feed several reductions at once instead of a write: per-channel minimum,
-// maximum and sum, and the maximum absolute value. Per thread, then per warp
-// (shuffles), then per block (shared memory), then one atomic per block and
-// statistic. Min/max travel as order-preserving unsigned keys; sums as
-// 64-bit fixed point (2^-20), so every accumulation is exact integer
-// arithmetic and the result does not depend on the order blocks finish.
+// maximum and sum (the maximum absolute value follows from the extremes).
+// A persistent grid of blocks walks jobs of blockDim.y rows x blockDim.x * V
+// columns of one image; every thread keeps its minima and maxima as floats
+// and its sums as 64-bit fixed point (2^-20; each job's V values are summed
+// in float32 first), then per warp (shuffles), per block (shared memory) and
+// one atomic per block and statistic. Min/max travel as order-preserving
+// unsigned keys and the sums are integers, so the result does not depend on
+// the order in which blocks finish.
 // ---------------------------------------------------------------------------
 struct ReduceAcc {
   unsigned int min_key[3];
   unsigned int max_key[3];
   unsigned long long sum_fx[3];  // two's complement fixed point, 2^-20 units
-  unsigned int absmax_key;
-  unsigned int _pad;
 };
 constexpr float kSumScale = 1048576.f;  // 2^20
 
@@ -36,54 +37,115 @@ struct ReduceArgs {
   typename RB::ParamsType rp;
   Cops cops;
   int32_t H, W_;
+  int32_t col_tiles;  // jobs per row band: ceil(ceil(W_ / V) / blockDim.x)
+  int32_t row_tiles;  // row bands per image: ceil(H / blockDim.y)
   ReduceAcc* acc;
 };
 
+// Whether the n outputs from (x0, y) of an image placed by resample
+// parameters all lie outside its window (the letterbox fill).
+FKL_D bool fill_span(const ResampleParams& p, int x0, int y, int n) {
+  const int lx = x0 - p.ox, ly = y - p.oy;
+  return ly < 0 || ly >= p.dh || lx + n <= 0 || lx >= p.dw;
+}
+
+// Folds n <= V chain values into the thread's extremes and sums.
+template <int V, class Cops>
+FKL_D void reduce_values(const Cops& cops, const F3 (&in)[V], int n, float (&mn)[3], float (&mx)[3],
+                         long long (&fx)[3]) {
+  float ps[3] = {0.f, 0.f, 0.f};
+  if constexpr (ChainHasPair<Cops>::value && V % 2 == 0) {
+    if (n == V) {
+#pragma unroll
+      for (int k = 0; k < V; k += 2) {
+        F3 v0, v1;
+        unpack_pair(apply_chain_pair(pack_pair(in[k], in[k + 1]), cops), v0, v1);
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+          mn[c] = fminf(mn[c], fminf(v0.v[c], v1.v[c]));
+          mx[c] = fmaxf(mx[c], fmaxf(v0.v[c], v1.v[c]));
+          ps[c] = __fadd_rn(__fadd_rn(ps[c], v0.v[c]), v1.v[c]);
+        }
+      }
+#pragma unroll
+      for (int c = 0; c < 3; ++c) fx[c] += __float2ll_rn(__fmul_rn(ps[c], kSumScale));
+      return;
+    }
+  }
+#pragma unroll
+  for (int k = 0; k < V; ++k) {
+    if (k < n) {
+      const auto v = apply_chain(in[k], cops);
+#pragma unroll
+      for (int c = 0; c < 3; ++c) {
+        mn[c] = fminf(mn[c], v.v[c]);
+        mx[c] = fmaxf(mx[c], v.v[c]);
+        ps[c] = __fadd_rn(ps[c], v.v[c]);
+      }
+    }
+  }
+#pragma unroll
+  for (int c = 0; c < 3; ++c) fx[c] += __float2ll_rn(__fmul_rn(ps[c], kSumScale));
+}
+
 template <int V, class RB, class Cops>
-__global__ void __launch_bounds__(256) reduce2d_kernel(const __grid_constant__ ReduceArgs<RB, Cops> a) {
+FKL_D void reduce_span(const ReduceArgs<RB, Cops>& a, int x0, int y, int z, float (&mn)[3], float (&mx)[3],
+                       long long (&fx)[3]) {
   using RT = typename RB::OutputType;
-  const int x0 = (blockIdx.x * blockDim.x + threadIdx.x) * V;
-  const int y = blockIdx.y * blockDim.y + threadIdx.y;
-  const int z = blockIdx.z;
-  float mn[3], mx[3], sm[3], am = 0.f;
+  static_assert(std::is_same_v<RT, F3>, "reductions run on three-channel float values");
+  const int n = min(V, a.W_ - x0);
+  if constexpr (std::is_same_v<std::decay_t<decltype(a.rp.p[0])>, ResampleParams>) {
+    const ResampleParams& q = a.rp.p[z];
+    if (fill_span(q, x0, y, n)) {  // n copies of one value: the chain runs once
+      const auto v = apply_chain(F3{{q.pad, q.pad, q.pad}}, a.cops);
+#pragma unroll
+      for (int c = 0; c < 3; ++c) {
+        mn[c] = fminf(mn[c], v.v[c]);
+        mx[c] = fmaxf(mx[c], v.v[c]);
+        fx[c] += __float2ll_rn(__fmul_rn(__fmul_rn(v.v[c], static_cast<float>(n)), kSumScale));
+      }
+      return;
+    }
+  }
+  RT in[V];
+  const Point pt{x0, y, z};
+  if (n == V) {
+    RB::template exec_span<V>(pt, a.rp, in);
+  } else {
+#pragma unroll
+    for (int k = 0; k < V; ++k)
+      if (k < n) in[k] = RB::exec(Point{x0 + k, y, z}, a.rp);
+  }
+  reduce_values<V>(a.cops, in, n, mn, mx, fx);
+}
+
+template <int V, class RB, class Cops>
+FKL_D void reduce2d_body(const ReduceArgs<RB, Cops>& a) {
+  float mn[3], mx[3];
+  long long fx[3];
 #pragma unroll
   for (int c = 0; c < 3; ++c) {
     mn[c] = __int_as_float(0x7f800000);
     mx[c] = -__int_as_float(0x7f800000);
-    sm[c] = 0.f;
+    fx[c] = 0;
   }
-  if (x0 < a.W_ && y < a.H && z < a.rp.count) {
-    const int n = min(V, a.W_ - x0);
-    RT in[V];
-    const Point pt{x0, y, z};
-    if (n == V) {
-      RB::template exec_span<V>(pt, a.rp, in);
-    } else {
-#pragma unroll
-      for (int k = 0; k < V; ++k)
-        if (k < n) in[k] = RB::exec(Point{x0 + k, y, z}, a.rp);
-    }
-#pragma unroll
-    for (int k = 0; k < V; ++k) {
-      if (k < n) {
-        const auto v = apply_chain(in[k], a.cops);
-#pragma unroll
-        for (int c = 0; c < 3; ++c) {
-          mn[c] = fminf(mn[c], v.v[c]);
-          mx[c] = fmaxf(mx[c], v.v[c]);
-          sm[c] = __fadd_rn(sm[c], v.v[c]);
-          am = fmaxf(am, fabsf(v.v[c]));
-        }
-      }
-    }
+  // jobs in (image, row band, column tile) order; the job index is the same
+  // for the whole block
+  const int per_image = a.col_tiles * a.row_tiles;
+  const int jobs = per_image * a.rp.count;
+  for (int job = blockIdx.x; job < jobs; job += gridDim.x) {
+    const int z = job / per_image;
+    const int r = job - z * per_image;
+    const int band = r / a.col_tiles;
+    const int x0 = ((r - band * a.col_tiles) * blockDim.x + threadIdx.x) * V;
+    const int y = band * blockDim.y + threadIdx.y;
+    if (x0 < a.W_ && y < a.H) reduce_span<V>(a, x0, y, z, mn, mx, fx);
   }
-  unsigned int kmin[3], kmax[3], kabs = order_key(am);
-  long long fx[3];
+  unsigned int kmin[3], kmax[3];
 #pragma unroll
   for (int c = 0; c < 3; ++c) {
     kmin[c] = order_key(mn[c]);
     kmax[c] = order_key(mx[c]);
-    fx[c] = __float2ll_rn(__fmul_rn(sm[c], kSumScale));
   }
 #pragma unroll
   for (int off = 16; off > 0; off >>= 1) {
@@ -93,9 +155,8 @@ __global__ void __launch_bounds__(256) reduce2d_kernel(const __grid_constant__ R
       kmax[c] = max(kmax[c], __shfl_xor_sync(0xffffffffu, kmax[c], off));
       fx[c] += __shfl_xor_sync(0xffffffffu, fx[c], off);
     }
-    kabs = max(kabs, __shfl_xor_sync(0xffffffffu, kabs, off));
   }
-  __shared__ unsigned int s_min[8][3], s_max[8][3], s_abs[8];
+  __shared__ unsigned int s_min[8][3], s_max[8][3];
   __shared__ long long s_sum[8][3];
   const int tid = threadIdx.y * blockDim.x + threadIdx.x;
   const int warp = tid >> 5, lane = tid & 31, nwarps = (blockDim.x * blockDim.y + 31) >> 5;
@@ -106,7 +167,6 @@ __global__ void __launch_bounds__(256) reduce2d_kernel(const __grid_constant__ R
       s_max[warp][c] = kmax[c];
       s_sum[warp][c] = fx[c];
     }
-    s_abs[warp] = kabs;
   }
   __syncthreads();
   if (tid == 0) {
@@ -117,7 +177,6 @@ __global__ void __launch_bounds__(256) reduce2d_kernel(const __grid_constant__ R
         kmax[c] = max(kmax[c], s_max[w][c]);
         fx[c] += s_sum[w][c];
       }
-      kabs = max(kabs, s_abs[w]);
     }
 #pragma unroll
     for (int c = 0; c < 3; ++c) {
@@ -125,8 +184,15 @@ __global__ void __launch_bounds__(256) reduce2d_kernel(const __grid_constant__ R
       atomicMax(&a.acc->max_key[c], kmax[c]);
       atomicAdd(&a.acc->sum_fx[c], static_cast<unsigned long long>(fx[c]));
     }
-    atomicMax(&a.acc->absmax_key, kabs);
   }
+}
+
+// kMinBlocks > 0 caps the registers so that many 256-thread blocks are
+// resident per SM (more loads in flight); 0 keeps the compiler's choice.
+template <int V, int kMinBlocks, class RB, class Cops>
+__global__ void __launch_bounds__(256, kMinBlocks > 0 ? kMinBlocks : 1)
+    reduce2d_kernel(const __grid_constant__ ReduceArgs<RB, Cops> a) {
+  reduce2d_body<V>(a);
 }
 
 }  // namespace fkl

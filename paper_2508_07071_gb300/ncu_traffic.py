@@ -9,7 +9,7 @@ figure only while that hash still matches).
 
     python -m paper_2508_07071_gb300.ncu_traffic --csv launches.csv \\
         --key nv12_letterbox_bf16_256 --kernel transform2d --unit k_nv12_bf16.cu \\
-        --command "<ncu command>"
+        [--header fkl/reduce.cuh] --command "<ncu command>"
 """
 from __future__ import annotations
 
@@ -88,9 +88,11 @@ def main() -> None:
     ap.add_argument("--kernel", default="transform2d", help="regular expression on the kernel name")
     ap.add_argument("--command", required=True, help="the ncu command line that wrote the CSV")
     ap.add_argument("--unit", required=True, help="translation unit of the kernel, relative to csrc/")
+    ap.add_argument("--header", action="append", default=[],
+                    help="a further header the kernel is defined in, relative to csrc/ (repeatable)")
     a = ap.parse_args()
     entry = summarise(parse_launches(a.csv, a.kernel))
-    entry["sources"] = sorted(DEVICE_HEADERS + [a.unit])
+    entry["sources"] = sorted(set(DEVICE_HEADERS + a.header + [a.unit]))
     entry["source_hash"] = source_hash(entry["sources"])
     entry["command"] = a.command
     data = json.load(open(TRAFFIC)) if os.path.exists(TRAFFIC) else {}
