@@ -50,6 +50,13 @@ struct HasPrepare : std::false_type {};
 template <class W>
 struct HasPrepare<W, std::void_t<decltype(&W::prepare)>> : std::true_type {};
 
+// A read may offer fill(pt, n, params, v): whether its n outputs from pt are
+// all one fill value v (the letterbox area of a placed image).
+template <class RB, class = void>
+struct HasFill : std::false_type {};
+template <class RB>
+struct HasFill<RB, std::void_t<decltype(&RB::fill)>> : std::true_type {};
+
 template <int V, int RY, class RB, class W, class Cops>
 FKL_D void transform2d_body(const Args2D<RB, W, Cops>& a) {
   using RT = typename RB::OutputType;
@@ -68,6 +75,21 @@ FKL_D void transform2d_body(const Args2D<RB, W, Cops>& a) {
       return a.wp;
     }
   }();
+
+  // A span wholly in the fill runs the chain once and writes that value V
+  // times (the same bits as the per-pixel path: every lane of a packed op
+  // rounds as the scalar op); the write's conversions collapse to one.
+  if constexpr (RY == 1 && HasFill<RB>::value) {
+    RT fv;
+    if (ybase < a.H && RB::fill(Point{x0, ybase, z}, n, a.rp, fv)) {
+      const WT o = apply_chain(fv, a.cops);
+      WT out[V];
+#pragma unroll
+      for (int k = 0; k < V; ++k) out[k] = o;
+      W::template exec_span<V>(Point{x0, ybase, z}, n, out, wp);
+      return;
+    }
+  }
 
   // Read every row first so that all loads of the thread are in flight
   // before the first store.

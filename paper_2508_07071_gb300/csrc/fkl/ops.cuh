@@ -35,6 +35,16 @@ static_assert(sizeof(ResampleParams) == 64, "kernel-parameter table entry");
 constexpr int32_t kFast2x = 1;   // exact 2x, even 16-byte aligned window: vector loads
 constexpr int32_t kExact2x = 2;  // rw == 2 dw and rh == 2 dh
 
+// Whether the n outputs from (x0, y) of an image placed by resample
+// parameters all lie outside its window, in the fill (letterbox) area.
+// Only reads that place an image (kPlaced: the pad value outside the
+// window) have such an area; the full-frame reads of the unfused chains
+// carry the same parameters with another meaning.
+FKL_HD bool fill_span(const ResampleParams& p, int x0, int y, int n) {
+  const int lx = x0 - p.ox, ly = y - p.oy;
+  return ly < 0 || ly >= p.dh || lx + n <= 0 || lx >= p.dw;
+}
+
 // Half-pixel sample along one axis for output index d (0 <= d < n_dst):
 // u = (d + 1/2) n_src / n_dst - 1/2 = num / D with num = (2d+1) n_src - n_dst
 // and D = 2 n_dst, clamped to [0, n_src - 1]. i0 = floor(u), i1 = min(i0 + 1,
@@ -132,6 +142,7 @@ struct ResizeU8C3T {
   using InstanceType = ReadType;
   using ParamsType = ResampleParams;
   using OutputType = F3;
+  static constexpr bool kPlaced = true;  // the pad value outside the placed window
 
   static FKL_D F3 blend(const uint8_t* row0, const uint8_t* row1, const AxisTap& tx,
                         int Dx, const AxisTap& ty, int Dy, float inv_area) {
@@ -277,6 +288,7 @@ struct ResizeNV12 {
   using InstanceType = ReadType;
   using ParamsType = ResampleParams;
   using OutputType = F3;
+  static constexpr bool kPlaced = true;  // the pad value outside the placed window
 
   static FKL_D F3 exec(const Point& pt, const ParamsType& p) {
     const int lx = pt.x - p.ox, ly = pt.y - p.oy;
@@ -395,6 +407,7 @@ struct ResizeNV12x2 {
   using InstanceType = ReadType;
   using ParamsType = ResampleParams;
   using OutputType = F3;
+  static constexpr bool kPlaced = true;  // the pad value outside the placed window
 
   static FKL_D F3 exec(const Point& pt, const ParamsType& p) {
     const int lx = pt.x - p.ox, ly = pt.y - p.oy;
@@ -448,6 +461,7 @@ struct ResizeF32C3T {
   using InstanceType = ReadType;
   using ParamsType = ResampleParams;
   using OutputType = F3;
+  static constexpr bool kPlaced = true;  // the pad value outside the placed window
   static FKL_D F3 load(const ParamsType& p, int sx, int sy) {
     const float* q = reinterpret_cast<const float*>(p.src + static_cast<int64_t>(sy) * p.pitch) + 3 * sx;
     return F3{{__ldg(q), __ldg(q + 1), __ldg(q + 2)}};
@@ -487,6 +501,12 @@ struct CropU8C3 {
   }
 };
 
+// Whether a read places its image in the output with a fill around it.
+template <class R, class = void>
+struct Placed : std::false_type {};
+template <class R>
+struct Placed<R, std::enable_if_t<R::kPlaced>> : std::true_type {};
+
 // Horizontal fusion (paper §IV-B, BatchRead): an array of per-image params
 // indexed by thread.z; `count` disables the unused entries.
 template <class ROp, int CAP>
@@ -502,6 +522,19 @@ struct BatchRead {
 
   static FKL_D OutputType exec(const Point& pt, const ParamsType& bp) {
     return ROp::exec(pt, bp.p[pt.z]);
+  }
+
+  // Whether the n outputs from pt are all the fill value of their image
+  // (then `v` is that value): placing reads only.
+  static FKL_D bool fill(const Point& pt, int n, const ParamsType& bp, OutputType& v) {
+    if constexpr (Placed<ROp>::value && std::is_same_v<OutputType, F3>) {
+      const ResampleParams& p = bp.p[pt.z];
+      if (fill_span(p, pt.x, pt.y, n)) {
+        v = F3{{p.pad, p.pad, p.pad}};
+        return true;
+      }
+    }
+    return false;
   }
 
   template <class R, int V, class = void>

@@ -42,13 +42,6 @@ struct ReduceArgs {
   ReduceAcc* acc;
 };
 
-// Whether the n outputs from (x0, y) of an image placed by resample
-// parameters all lie outside its window (the letterbox fill).
-FKL_D bool fill_span(const ResampleParams& p, int x0, int y, int n) {
-  const int lx = x0 - p.ox, ly = y - p.oy;
-  return ly < 0 || ly >= p.dh || lx + n <= 0 || lx >= p.dw;
-}
-
 // Folds n <= V chain values into the thread's extremes and sums.
 template <int V, class Cops>
 FKL_D void reduce_values(const Cops& cops, const F3 (&in)[V], int n, float (&mn)[3], float (&mx)[3],
@@ -94,7 +87,7 @@ FKL_D void reduce_span(const ReduceArgs<RB, Cops>& a, int x0, int y, int z, floa
   using RT = typename RB::OutputType;
   static_assert(std::is_same_v<RT, F3>, "reductions run on three-channel float values");
   const int n = min(V, a.W_ - x0);
-  if constexpr (std::is_same_v<std::decay_t<decltype(a.rp.p[0])>, ResampleParams>) {
+  if constexpr (Placed<typename RB::Op>::value) {
     const ResampleParams& q = a.rp.p[z];
     if (fill_span(q, x0, y, n)) {  // n copies of one value: the chain runs once
       const auto v = apply_chain(F3{{q.pad, q.pad, q.pad}}, a.cops);
