@@ -870,3 +870,38 @@ def test_typed_chain_replays_in_a_cuda_graph(F, W):
     torch.cuda.synchronize()
     want = np.concatenate([O.typed_chain(x.cpu().numpy(), "bf16", 1 / 3, 0.25, 0.5) for x in xs])
     assert np.array_equal(_decode(F, out, "bf16"), want)
+
+
+@pytest.mark.parametrize("fmt", ["f32", "e4m3"])
+@pytest.mark.parametrize("src", ["nv12", "packed"])
+def test_pillarbox_fill_columns_every_shape(F, W, src, fmt):
+    """A portrait image letterboxed into a square: fill columns left and right.
+    Spans wholly in the fill run the chain once, spans across the window edge
+    mix fill and image pixels; every launch shape, the unfused form and the
+    oracle agree."""
+    ow = oh = 128
+    scale = W.E4M3_SCALE if fmt == "e4m3" else None
+    if src == "nv12":
+        frames = synth.nv12_frames(23, 2, 320, 180)        # window 72 x 128 at x = 28
+        srcs = [torch.from_numpy(frames[i]).cuda() for i in range(2)]
+        layout, read = F.FKL_LAYOUT_NV12, F.read_nv12()
+        rgb = [O.nv12_to_rgb(frames[i]) for i in range(2)]
+    else:
+        imgs = [synth.packed_image(24 + i, 300, 170) for i in range(2)]   # window 73 x 128 at x = 27
+        srcs = [torch.from_numpy(im).cuda() for im in imgs]
+        layout, read = None, F.read_u8c3()
+        rgb = [im.astype(np.float64) for im in imgs]
+    ops = [read, F.letterbox(ow, oh, 114.0), F.mul(W.INV255), F.write_split(code(F, fmt), scale)]
+    base = run_batch(F, ops, srcs, None, (2, 3, oh, ow), fmt, layout_in=layout)
+    unf = run_batch(F, ops, srcs, None, (2, 3, oh, ow), fmt, layout_in=layout, unfused=True)
+    assert torch.equal(base.view(torch.uint8), unf.view(torch.uint8))
+    p = F.Pipeline(ops)
+    for shape in F.fkl_pipeline_shapes(p.handle):
+        got = run_batch(F, ops, srcs, None, (2, 3, oh, ow), fmt, layout_in=layout, shape=shape)
+        assert torch.equal(got.view(torch.uint8), base.view(torch.uint8)), shape
+    F.fkl_device_check()
+    for i in range(2):
+        want = O.split(O.multiply(O.letterbox(rgb[i], ow, oh, 114.0), 1 / 255))
+        check_output(base[i], want, fmt, W.E4M3_SCALE if fmt == "e4m3" else 1.0, f"pillarbox {src} {fmt}")
+        cols = O.letterbox_geometry(rgb[i].shape[1], rgb[i].shape[0], ow, oh)
+        assert cols[2] > 0, "the window is inset: there are fill columns"
