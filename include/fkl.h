@@ -480,9 +480,11 @@ FKL_API fkl_status fkl_pipeline_shape_at(fkl_pipeline p, int32_t k,
  * Autotuner (tile, coarsening and block shape): runs every launch shape
  * fkl_pipeline_shape_at lists on these arguments -- one warm-up launch, then
  * `reps` (1..32) launches enqueued back to back, each timed with its own pair
- * of CUDA events on `stream` -- and keeps the shape with the lowest median
- * as the pipeline's shape. `best` and `best_us` (median microseconds per
- * launch, may be NULL) report it. Every trial writes `out`. Synchronises `stream`;
+ * of CUDA events on `stream` -- then times the shapes within 3% of the
+ * fastest median again (at most four, three rounds that visit each in turn,
+ * so that a drift in the GPU's speed hits them alike) and keeps the one with
+ * the lowest median of its round medians as the pipeline's shape. `best` and
+ * `best_us` (median microseconds per launch, may be NULL) report it. Every trial writes `out`. Synchronises `stream`;
  * not capturable in a CUDA graph. A pipeline with a single shape returns it
  * without timing.
  * fkl_pipeline_autotune_ex: the same, but calls `before(user)` on the host

@@ -9,6 +9,8 @@
 #include <mutex>
 #include <new>
 #include <string>
+#include <utility>
+#include <vector>
 
 #include "fkl/reduce.cuh"
 #include "registry.h"
@@ -916,6 +918,9 @@ fkl_status fkl_pipeline_autotune_ex(fkl_pipeline p, int32_t n, const fkl_tensor*
                                     fkl_tensor* out, void* stream, int32_t reps, void (*before)(void*), void* user,
                                     fkl_launch_shape* best, float* best_us) {
   constexpr int kMaxReps = 32;
+  constexpr int kFinalists = 4;      // re-timed: the shapes within 3% of the fastest
+  constexpr float kFinalSlack = 1.03f;
+  constexpr int kRounds = 3;         // interleaved, so that drift hits every finalist alike
   if (!p) return fail(FKL_ERR_INVALID, "null pipeline");
   if (reps < 1 || reps > kMaxReps) return fail(FKL_ERR_INVALID, "reps must be in 1..%d", kMaxReps);
   auto run = [&]() -> fkl_status { return fkl_execute_batch(p, n, ins, rois, out, stream); };
@@ -933,8 +938,9 @@ fkl_status fkl_pipeline_autotune_ex(fkl_pipeline p, int32_t n, const fkl_tensor*
     int made = 0;
     for (; made < 2 * reps && ce == cudaSuccess; ++made) ce = cudaEventCreate(&ev[made]);
     fkl_status st = FKL_OK;
-    for (size_t k = 0; k < shapes.size() && ce == cudaSuccess && st == FKL_OK; ++k) {
-      p->shape = shapes[k];
+    // median microseconds of `reps` launches with shape k (after one warm-up)
+    auto time_shape = [&](const fkl_launch_shape& shape, float& us) -> bool {
+      p->shape = shape;
       st = run();
       for (int r = 0; r < reps && st == FKL_OK && ce == cudaSuccess; ++r) {
         if (before) before(user);
@@ -942,16 +948,47 @@ fkl_status fkl_pipeline_autotune_ex(fkl_pipeline p, int32_t n, const fkl_tensor*
         st = run();
         if (st == FKL_OK) ce = cudaEventRecord(ev[2 * r + 1], s);
       }
-      if (st != FKL_OK || ce != cudaSuccess) break;
-      if ((ce = cudaEventSynchronize(ev[2 * reps - 1])) != cudaSuccess) break;
+      if (st != FKL_OK || ce != cudaSuccess) return false;
+      if ((ce = cudaEventSynchronize(ev[2 * reps - 1])) != cudaSuccess) return false;
       float t[kMaxReps];
       for (int r = 0; r < reps && ce == cudaSuccess; ++r) ce = cudaEventElapsedTime(&t[r], ev[2 * r], ev[2 * r + 1]);
-      if (ce != cudaSuccess) break;
+      if (ce != cudaSuccess) return false;
       std::sort(t, t + reps);
-      const float us = 1000.f * t[reps / 2];
-      if (best_t < 0.f || us < best_t) {
-        best_t = us;
-        best_s = shapes[k];
+      us = 1000.f * t[reps / 2];
+      return true;
+    };
+    std::vector<std::pair<float, size_t>> first;  // (median, shape index)
+    bool ok = ce == cudaSuccess;
+    for (size_t k = 0; k < shapes.size() && ok; ++k) {
+      float us = 0.f;
+      ok = time_shape(shapes[k], us);
+      if (ok) first.emplace_back(us, k);
+    }
+    if (ok && !first.empty()) {
+      std::sort(first.begin(), first.end());
+      std::vector<size_t> fin;
+      for (const auto& f : first)
+        if (fin.size() < kFinalists && f.first <= first[0].first * kFinalSlack) fin.push_back(f.second);
+      best_t = first[0].first;
+      best_s = shapes[first[0].second];
+      if (fin.size() > 1) {
+        std::vector<std::vector<float>> rounds(fin.size());
+        for (int r = 0; r < kRounds && ok; ++r)
+          for (size_t i = 0; i < fin.size() && ok; ++i) {
+            float us = 0.f;
+            ok = time_shape(shapes[fin[i]], us);
+            if (ok) rounds[i].push_back(us);
+          }
+        if (ok) {
+          for (size_t i = 0; i < fin.size(); ++i) {
+            std::sort(rounds[i].begin(), rounds[i].end());
+            const float us = rounds[i][rounds[i].size() / 2];
+            if (i == 0 || us < best_t) {
+              best_t = us;
+              best_s = shapes[fin[i]];
+            }
+          }
+        }
       }
     }
     for (int i = 0; i < made; ++i)
