@@ -126,7 +126,6 @@ FKL_D void reduce2d_body(const ReduceArgs<RB, Cops>& a) {
   // for the whole block
   const int per_image = a.col_tiles * a.row_tiles;
   const int jobs = per_image * a.rp.count;
-#pragma unroll 1
   for (int job = blockIdx.x; job < jobs; job += gridDim.x) {
     const int z = job / per_image;
     const int r = job - z * per_image;
