@@ -444,8 +444,8 @@ FKL_API const char* fkl_pipeline_kernel_name(fkl_pipeline p);
 /* Launch shape used by the fused kernel.
  * Image chains: V output pixels per thread along x, a TX x TY thread block
  * (TX * TY <= 256), RY output rows per thread.
- * Float32 tensor chains: `vec` elements per thread and iteration (4, 8, 16
- * or 32), TX threads per block (TY = 1); RY = 1 runs a persistent grid of
+ * Float32 tensor chains: `vec` elements per thread and iteration (2, 4, 8,
+ * 16 or 32), TX threads per block (TY = 1); RY = 1 runs a persistent grid of
  * (2048 / TX) blocks per SM striding over the tensor, RY = 0 one block per
  * TX * vec elements.
  * NV12 chains with a split output, RY <= 0: the row-staged kernel (paper

@@ -471,10 +471,10 @@ std::vector<fkl_launch_shape> shapes_for(const Spec& s) {
       vecs = {8, 16};
   } else {
     std::vector<fkl_launch_shape> out;
-    // 4 elements per thread spread a small tensor over more warps: an
+    // 2 or 4 elements per thread spread a small tensor over more warps: an
     // ALU-bound chain ends when the most loaded warp scheduler (4 per SM)
     // does, so finer warps balance better
-    for (int v : {4, 8, 16, 32})
+    for (int v : {2, 4, 8, 16, 32})
       for (int tx : {128, 256, 512})
         for (int ry : {1, 0}) out.push_back(fkl_launch_shape{v, tx, 1, ry});
     return out;

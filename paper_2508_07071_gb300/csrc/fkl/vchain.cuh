@@ -7,9 +7,10 @@ namespace fkl {
 // ---------------------------------------------------------------------------
 // Linear TransformDPP for 1-D float tensors (the vertical Mul/Add chain of
 // paper §VI-B/§VI-G). The chain is a table of constants plus a bitmask of op
-// kinds held in the kernel parameters; each thread keeps U float4 vectors in
-// registers and applies every op to all of them before the next op, so the
-// dependent chain of one element is interleaved with 4U - 1 independent ones.
+// kinds held in the kernel parameters; each thread keeps E elements (2 or a
+// multiple of 4, loaded as one float2 or as float4 vectors) in registers
+// and applies every op to all of them before the next op, so the dependent
+// chain of one element is interleaved with E - 1 independent ones.
 // ---------------------------------------------------------------------------
 template <int CAP>
 struct VChainParams {
@@ -29,7 +30,15 @@ template <class InT, int E>
 FKL_D void vchain_load(const void* in, int64_t base, int64_t n, bool vec, float (&x)[E]) {
   if constexpr (std::is_same_v<InT, float>) {
     const float* f = static_cast<const float*>(in);
-    if (vec) {
+    if constexpr (E == 2) {
+      if (vec) {
+        const float2 v = __ldcs(reinterpret_cast<const float2*>(f + base));
+        x[0] = v.x;
+        x[1] = v.y;
+        return;
+      }
+    }
+    if (vec && E % 4 == 0) {
 #pragma unroll
       for (int u = 0; u < E / 4; ++u) {
         const float4 v = __ldcs(reinterpret_cast<const float4*>(f + base) + u);
@@ -43,11 +52,14 @@ FKL_D void vchain_load(const void* in, int64_t base, int64_t n, bool vec, float 
       for (int e = 0; e < E; ++e) x[e] = base + e < n ? f[base + e] : 0.f;
     }
   } else {
-    static_assert(std::is_same_v<InT, uint8_t> && (E == 4 || E % 8 == 0), "u8 chains load 4 or 8-byte multiples");
+    static_assert(std::is_same_v<InT, uint8_t> && (E == 2 || E == 4 || E % 8 == 0),
+                  "u8 chains load 2, 4 or 8-byte multiples");
     const uint8_t* b = static_cast<const uint8_t*>(in);
     if (vec) {
-      uint32_t w[E / 4];
-      if constexpr (E == 4) {
+      uint32_t w[(E + 3) / 4];
+      if constexpr (E == 2) {
+        w[0] = __ldcs(reinterpret_cast<const unsigned short*>(b + base));
+      } else if constexpr (E == 4) {
         w[0] = __ldcs(reinterpret_cast<const unsigned int*>(b + base));
       } else if constexpr (E == 8) {
         const uint2 v = __ldcs(reinterpret_cast<const uint2*>(b + base));
@@ -72,9 +84,9 @@ FKL_D void vchain_load(const void* in, int64_t base, int64_t n, bool vec, float 
   }
 }
 
-template <int U, int CAP, bool kAlt, class InT = float>
+template <int E, int CAP, bool kAlt, class InT = float>
 __global__ void __launch_bounds__(512) vchain_kernel(const __grid_constant__ VChainParams<CAP> p) {
-  constexpr int E = 4 * U;  // elements per thread
+  static_assert(E == 2 || E % 4 == 0, "2 or a multiple of 4 elements per thread");
   constexpr int kInBytes = static_cast<int>(sizeof(InT));
   const int64_t stride = static_cast<int64_t>(gridDim.x) * blockDim.x * E;
   for (int64_t base = (static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x) * E; base < p.n;
@@ -125,10 +137,14 @@ __global__ void __launch_bounds__(512) vchain_kernel(const __grid_constant__ VCh
       }
     }
     if (full) {
+      if constexpr (E == 2) {
+        __stcs(reinterpret_cast<float2*>(p.out + base), make_float2(x[0], x[1]));
+      } else {
 #pragma unroll
-      for (int u = 0; u < U; ++u)
-        __stcs(reinterpret_cast<float4*>(p.out + base) + u,
-               make_float4(x[4 * u], x[4 * u + 1], x[4 * u + 2], x[4 * u + 3]));
+        for (int u = 0; u < E / 4; ++u)
+          __stcs(reinterpret_cast<float4*>(p.out + base) + u,
+                 make_float4(x[4 * u], x[4 * u + 1], x[4 * u + 2], x[4 * u + 3]));
+      }
     } else {
 #pragma unroll
       for (int e = 0; e < E; ++e)

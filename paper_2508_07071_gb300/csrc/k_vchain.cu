@@ -11,10 +11,10 @@ namespace fkl_impl {
 
 namespace {
 
-constexpr int kDefaultU = 4;  // float4 vectors per thread
+constexpr int kDefaultE = 16;  // elements per thread
 constexpr int kDefaultBlock = 256;
 
-template <int U, int CAP>
+template <int E, int CAP>
 cudaError_t run_chunk(const Spec& s, size_t start, int len, const void* in, bool in_u8, float* out, int64_t n,
                       int block, bool persistent, cudaStream_t st) {
   fkl::VChainParams<CAP> p;
@@ -31,20 +31,20 @@ cudaError_t run_chunk(const Spec& s, size_t start, int len, const void* in, bool
     if (kind != (i & 1)) alt = false;
   }
   p.alternating = alt ? 1 : 0;
-  const int64_t per_block = static_cast<int64_t>(block) * 4 * U;
+  const int64_t per_block = static_cast<int64_t>(block) * E;
   const int64_t need = std::max<int64_t>(1, (n + per_block - 1) / per_block);
   const int64_t cap = persistent ? int64_t(sm_count()) * std::max(1, 2048 / block) : need;
   const int blocks = static_cast<int>(std::min<int64_t>(need, std::min<int64_t>(cap, 0x7fffffff)));
   if (in_u8) {
     if (alt)
-      fkl::vchain_kernel<U, CAP, true, uint8_t><<<blocks, block, 0, st>>>(p);
+      fkl::vchain_kernel<E, CAP, true, uint8_t><<<blocks, block, 0, st>>>(p);
     else
-      fkl::vchain_kernel<U, CAP, false, uint8_t><<<blocks, block, 0, st>>>(p);
+      fkl::vchain_kernel<E, CAP, false, uint8_t><<<blocks, block, 0, st>>>(p);
   } else {
     if (alt)
-      fkl::vchain_kernel<U, CAP, true><<<blocks, block, 0, st>>>(p);
+      fkl::vchain_kernel<E, CAP, true><<<blocks, block, 0, st>>>(p);
     else
-      fkl::vchain_kernel<U, CAP, false><<<blocks, block, 0, st>>>(p);
+      fkl::vchain_kernel<E, CAP, false><<<blocks, block, 0, st>>>(p);
   }
   return cudaGetLastError();
 }
@@ -54,14 +54,16 @@ cudaError_t run_shape(const Spec& s, const fkl_launch_shape& sh, size_t start, i
                       float* out, int64_t n, cudaStream_t st) {
   const bool persistent = sh.ry != 0;
   switch (sh.vec) {
-    case 4:
-      return run_chunk<1, CAP>(s, start, len, in, in_u8, out, n, sh.tx, persistent, st);
-    case 8:
+    case 2:
       return run_chunk<2, CAP>(s, start, len, in, in_u8, out, n, sh.tx, persistent, st);
-    case 16:
+    case 4:
       return run_chunk<4, CAP>(s, start, len, in, in_u8, out, n, sh.tx, persistent, st);
-    case 32:
+    case 8:
       return run_chunk<8, CAP>(s, start, len, in, in_u8, out, n, sh.tx, persistent, st);
+    case 16:
+      return run_chunk<16, CAP>(s, start, len, in, in_u8, out, n, sh.tx, persistent, st);
+    case 32:
+      return run_chunk<32, CAP>(s, start, len, in, in_u8, out, n, sh.tx, persistent, st);
     default:
       return cudaErrorInvalidConfiguration;
   }
@@ -87,9 +89,9 @@ cudaError_t launch_vchain(const Spec& s, const fkl_launch_shape& sh, const void*
 // Unfused form: one kernel per op over the whole tensor.
 cudaError_t launch_unfused_vchain(const Spec& s, const void* in, float* out, int64_t n, cudaStream_t st) {
   const size_t L = s.vkinds.size();
-  if (L == 0) return run_chunk<kDefaultU, 8>(s, 0, 0, in, s.vinput_u8, out, n, kDefaultBlock, true, st);
+  if (L == 0) return run_chunk<kDefaultE, 8>(s, 0, 0, in, s.vinput_u8, out, n, kDefaultBlock, true, st);
   for (size_t i = 0; i < L; ++i) {
-    const cudaError_t e = run_chunk<kDefaultU, 8>(s, i, 1, i == 0 ? in : out, i == 0 && s.vinput_u8, out, n,
+    const cudaError_t e = run_chunk<kDefaultE, 8>(s, i, 1, i == 0 ? in : out, i == 0 && s.vinput_u8, out, n,
                                                   kDefaultBlock, true, st);
     if (e != cudaSuccess) return e;
   }
