@@ -251,6 +251,13 @@ FKL_D F3 scale255(const F3& u) {
 
 constexpr float k2p23 = 8388608.f;
 
+// The 2x span's constants as packed pairs in constant memory (both lanes
+// equal): the packed instructions read them from the constant bank rather
+// than from registers rebuilt for every use.
+static __constant__ __align__(8) float kNv12Pairs[16] = {
+    k2p23 + 16.f, k2p23 + 16.f,   k2p23 + 128.f, k2p23 + 128.f, Bt601::cy,  Bt601::cy,  Bt601::crv, Bt601::crv,
+    Bt601::cgu,   Bt601::cgu,     Bt601::cgv,    Bt601::cgv,    Bt601::cbu, Bt601::cbu, 63.75f,     63.75f};
+
 // 2^23 + (byte k of w), exactly, as a float: the byte is placed in the
 // mantissa of 2^23 by one byte permute; subtracting 2^23 + bias later gives
 // byte - bias exactly.
@@ -350,9 +357,9 @@ struct ResizeNV12 {
   template <int V>
   static FKL_D void compute2x(const uint4 (&a)[V / 8], const uint4 (&b)[V / 8], const uint4 (&c)[V / 8],
                               F3 (&out)[V]) {
-    const F2 kY = f2s(k2p23 + 16.f), kC = f2s(k2p23 + 128.f);
-    const F2 cy = f2s(Bt601::cy), crv = f2s(Bt601::crv), cgu = f2s(Bt601::cgu), cgv = f2s(Bt601::cgv),
-             cbu = f2s(Bt601::cbu), c6375 = f2s(63.75f);
+    const F2* kp = reinterpret_cast<const F2*>(kNv12Pairs);
+    const F2 kY = kp[0], kC = kp[1], cy = kp[2], crv = kp[3], cgu = kp[4], cgv = kp[5], cbu = kp[6],
+             c6375 = kp[7];
 #pragma unroll
     for (int k = 0; k < V; k += 2) {
       // outputs k, k+1 use bytes 2k .. 2k+3 of each row: word (k % 8) / 2 of
