@@ -45,3 +45,28 @@ def test_committed_traffic_file_is_well_formed():
         assert len(e["source_hash"]) == 16 and e["command"].startswith("ncu ")
         for rel in e.get("sources", []):
             assert os.path.exists(os.path.join(T.PKG, "csrc", rel)), rel
+
+
+def test_cli_records_the_kernel_headers(tmp_path, monkeypatch):
+    """--header adds the files a kernel is defined in to the hashed sources."""
+    import sys
+    k = "void fkl::reduce2d_kernel<16, 0, X>(ReduceArgs<T3, T4>)"
+    lines = [HEAD, row(0, k, "dram__bytes_read.sum", "byte", 400), row(0, k, "dram__bytes_write.sum", "byte", 4),
+             row(0, k, "gpu__time_duration.sum", "ns", "1,000")]
+    csv_path = tmp_path / "l.csv"
+    csv_path.write_text("".join(lines))
+    out = tmp_path / "traffic.json"
+    out.write_text('{"other": {"kept": true}}')
+    monkeypatch.setattr(T, "TRAFFIC", str(out))
+    monkeypatch.setattr(sys, "argv", ["ncu_traffic", "--csv", str(csv_path), "--key", "r", "--kernel", "reduce2d",
+                                      "--unit", "k_reduce.cu", "--header", "fkl/reduce.cuh",
+                                      "--command", "ncu --metrics x"])
+    T.main()
+    d = json.load(open(out))
+    assert d["other"] == {"kept": True}                      # other entries survive
+    e = d["r"]
+    assert e["dram_bytes_per_launch"] == 404 and e["launches"] == 1
+    assert "fkl/reduce.cuh" in e["sources"] and "k_reduce.cu" in e["sources"]
+    assert set(T.DEVICE_HEADERS) <= set(e["sources"])
+    assert e["source_hash"] == T.entry_hash(e)
+    assert e["source_hash"] != T.source_hash([s for s in e["sources"] if s != "fkl/reduce.cuh"])
