@@ -284,7 +284,8 @@ FKL_API fkl_status fkl_execute_batch_unfused_static(fkl_pipeline p, int32_t n, c
  * only (READ_U8C3 / READ_NV12 with a resize or letterbox). Launches: two
  * memsets, one reduction launch per 256 images and one finishing kernel.
  * Min/max are exact; the mean is accumulated in 64-bit fixed point
- * (2^-20), independent of the order in which blocks finish.
+ * (2^-20), independent of the order in which blocks finish. An empty batch
+ * (n = 0) leaves NaN extremes, mean 0, amax 0 and s = 1.
  */
 #define FKL_REDUCE_STATS_BYTES 128
 FKL_API fkl_status fkl_reduce_batch(fkl_pipeline p, int32_t n, const fkl_tensor* ins, const int32_t* rois,

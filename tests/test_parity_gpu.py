@@ -905,3 +905,14 @@ def test_pillarbox_fill_columns_every_shape(F, W, src, fmt):
         check_output(base[i], want, fmt, W.E4M3_SCALE if fmt == "e4m3" else 1.0, f"pillarbox {src} {fmt}")
         cols = O.letterbox_geometry(rgb[i].shape[1], rgb[i].shape[0], ow, oh)
         assert cols[2] > 0, "the window is inset: there are fill columns"
+
+
+def test_reduce_empty_batch_gives_the_documented_stats(F, W):
+    p = F.Pipeline(W.nv12_letterbox_chain(F.FKL_E4M3, scale=1.0))
+    out = torch.zeros((1, 3, 640, 640), dtype=torch.float8_e4m3fn, device="cuda")   # fixes the size only
+    stats = torch.full((32,), 7.0, device="cuda")
+    F.fkl_reduce_batch(p.handle, [], None, F.as_fkl(out, F.FKL_LAYOUT_NCHW), stats.data_ptr())
+    torch.cuda.synchronize()
+    st = stats.cpu().numpy()
+    assert np.isnan(st[0:6]).all()                      # no value: no extremes
+    assert (st[6:9] == 0).all() and st[9] == 0 and st[10] == 1 and st[11] == 1
