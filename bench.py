@@ -225,7 +225,7 @@ class PackedBatch(Workload):
         self.host_out.copy_(self.dst, non_blocking=True)
 
     def oracle_sample(self, O, k):
-        import paper_2508_07071_gb300.workloads as W
+        import paper_2508_07071_gb300.configs as W
         r = self.rois[k % self.n]
         O.preprocess_packed(self.src_host, r, self.ow, self.oh, swap=True, mul=1 / 255,
                             sub=W.IMAGENET_MEAN, div=W.IMAGENET_STD)
@@ -510,7 +510,7 @@ def _oracle_worker_init(kind, params):
     """Builds one worker's inputs (the workload's seeded generators) and the
     oracle call of one unit; runs in a spawned process."""
     import oracle as O
-    from paper_2508_07071_gb300 import synth, workloads as W
+    from paper_2508_07071_gb300 import configs as W, synth  # no CUDA library in the workers
     if kind == "nv12":
         frames = synth.nv12_frames(params["seed"], 4, params["h"], params["w"])
         _WORKER["f"] = lambda k: O.preprocess_nv12(frames[k % 4], params["out"], params["out"], pad=114.0,
@@ -843,7 +843,7 @@ def run_reference(args):
     if rank != 0:
         return
     import multiprocessing as mp
-    from paper_2508_07071_gb300 import workloads as W, metrics
+    from paper_2508_07071_gb300 import configs as W, metrics  # the oracle arm needs no CUDA library
 
     cfg = W.NV12
     if args.workload != "nv12":

@@ -32,11 +32,15 @@ def test_sector_footprints():
 
 
 def test_reference_arm_prints_the_contract_line():
+    """The oracle arm runs without the CUDA library: the binding module is
+    made unimportable in the parent before bench.py starts."""
     import json
     import subprocess
     root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
-    r = subprocess.run([sys.executable, "bench.py", "--impl", "reference", "--steps", "2", "--warmup", "3"],
-                       cwd=root, capture_output=True, text=True, timeout=600)
+    run = ("import runpy, sys; sys.modules['paper_2508_07071_gb300.fkl'] = None; "
+           "sys.argv = ['bench.py', '--impl', 'reference', '--steps', '2', '--warmup', '3']; "
+           "runpy.run_path('bench.py', run_name='__main__')")
+    r = subprocess.run([sys.executable, "-c", run], cwd=root, capture_output=True, text=True, timeout=600)
     assert r.returncode == 0, r.stderr[-2000:]
     line = json.loads([l for l in r.stdout.splitlines() if l.startswith("{")][-1])
     for key in ("metric", "value", "unit", "n_gpus", "steps", "warmup", "ms_per_step", "higher_is_better",
