@@ -49,3 +49,18 @@ def test_reference_arm_prints_the_contract_line():
     assert line["impl"] == "reference" and line["value"] > 0 and line["unit"] == "GB/s"
     assert line["cpu_baseline"]["kind"] == "oracle" and line["cpu_baseline"]["cores"] >= 1
     assert line["e2e"]["h2d_bytes_per_step"] == 0 and line["e2e"]["value"] == line["value"]
+
+
+def test_workload_constants_live_in_the_library_free_module():
+    """configs.py holds the shapes without touching the CUDA binding, and
+    workloads.py re-exports the very same objects."""
+    import subprocess
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    code = ("import sys; import paper_2508_07071_gb300.configs as C; "
+            "assert 'paper_2508_07071_gb300.fkl' not in sys.modules; print(C.NV12['n'])")
+    r = subprocess.run([sys.executable, "-c", code], cwd=root, capture_output=True, text=True, timeout=120)
+    assert r.returncode == 0 and r.stdout.strip() == "256", r.stderr[-1000:]
+    from paper_2508_07071_gb300 import configs as C, workloads as W
+    for name in ("IMAGENET_MEAN", "IMAGENET_STD", "INV255", "E4M3_SCALE", "SINGLE", "HF", "VCHAIN", "NV12",
+                 "SERVE", "DTYPES"):
+        assert getattr(W, name) is getattr(C, name), name
