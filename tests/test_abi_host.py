@@ -162,11 +162,17 @@ def test_execute_validates_before_launch(F):
             "wrong layout": (src, F._tensor(0x2000, (1, 8, 16, 3), 192, F.FKL_F32, F.FKL_LAYOUT_NHWC)),
             "two channels": (F._tensor(0x1000, (20, 40, 2), 80, F.FKL_U8, F.FKL_LAYOUT_HWC), out),
             "input pitch": (F._tensor(0x1000, (20, 40, 3), 100, F.FKL_U8, F.FKL_LAYOUT_HWC), out),
+            "input wider than 16384": (F._tensor(0x1000, (20, 16385, 3), 3 * 16385, F.FKL_U8, F.FKL_LAYOUT_HWC),
+                                       out),
         }
         for name, (i, o) in bad.items():
             with pytest.raises(F.FklError) as ei:
                 F.fkl_execute(p, i, o, stream=0)
             assert ei.value.status == F.FKL_ERR_INVALID, name
+        # a resize target beyond 16384 is refused when the pipeline is made
+        with pytest.raises(F.FklError) as ei:
+            F.fkl_pipeline_create(W.normalize_chain(16385, 8))
+        assert ei.value.status == F.FKL_ERR_INVALID
         # batch: per-image ROIs validated too, out must hold n images
         with pytest.raises(F.FklError):
             F.fkl_execute_batch(p, [src, src], [(0, 0, 32, 16), (30, 0, 32, 16)], out, stream=0)

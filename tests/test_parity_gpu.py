@@ -916,3 +916,27 @@ def test_reduce_empty_batch_gives_the_documented_stats(F, W):
     st = stats.cpu().numpy()
     assert np.isnan(st[0:6]).all()                      # no value: no extremes
     assert (st[6:9] == 0).all() and st[9] == 0 and st[10] == 1 and st[11] == 1
+
+
+def test_largest_dimension(F, W):
+    """16384 pixels along a row, the largest size the ABI accepts: the packed
+    reader (general resize) and the NV12 exact-2x vector path agree with the
+    oracle and with their unfused forms."""
+    src = synth.packed_image(25, 64, 16384)
+    ops = W.normalize_chain(16384, 32)                    # 1x horizontally, 2x vertically
+    d = torch.from_numpy(src).cuda()
+    got = run_batch(F, ops, [d], None, (1, 3, 32, 16384), "f32")
+    unf = run_batch(F, ops, [d], None, (1, 3, 32, 16384), "f32", unfused=True)
+    assert torch.equal(got.view(torch.int32), unf.view(torch.int32))
+    want = O.preprocess_packed(src, (0, 0, 16384, 64), 16384, 32, swap=True, mul=1 / 255,
+                               sub=W.IMAGENET_MEAN, div=W.IMAGENET_STD)
+    check_f32(to_numpy(got)[0], want, "16384-wide packed")
+
+    frames = synth.nv12_frames(26, 1, 64, 16384)
+    ops = [F.read_nv12(), F.resize(8192, 32), F.mul(W.INV255), F.write_split(F.FKL_BF16)]
+    dev = torch.from_numpy(frames).cuda()
+    got = run_batch(F, ops, [dev[0]], None, (1, 3, 32, 8192), "bf16", layout_in=F.FKL_LAYOUT_NV12)
+    unf = run_batch(F, ops, [dev[0]], None, (1, 3, 32, 8192), "bf16", layout_in=F.FKL_LAYOUT_NV12, unfused=True)
+    assert torch.equal(got.view(torch.int16), unf.view(torch.int16))
+    want = O.split(O.multiply(O.resize_bilinear(O.nv12_to_rgb(frames[0]), 8192, 32), 1 / 255))
+    check_output(got[0], want, "bf16", 1.0, "16384-wide NV12")
