@@ -209,6 +209,8 @@ def test_nv12_full_batch_sampled(F, W):
     ((480, 640), 640, None),                   # upscale
     ((96, 130), 64, [(3, 5, 101, 77)]),        # odd crop offsets and sizes
     ((64, 48), 32, [(16, 8, 32, 40)]),         # 2x with 16-aligned crop: vector path
+    ((2, 2), 1, None),                         # smallest frame, 1x1 output (exact 2x)
+    ((2, 6), 3, None),                         # 3x1 window, fill rows above and below
 ])
 def test_nv12_general_geometry(F, W, hw, out, roi):
     frames = synth.nv12_frames(4, 1, *hw)
