@@ -942,3 +942,34 @@ def test_largest_dimension(F, W):
     assert torch.equal(got.view(torch.int16), unf.view(torch.int16))
     want = O.split(O.multiply(O.resize_bilinear(O.nv12_to_rgb(frames[0]), 8192, 32), 1 / 255))
     check_output(got[0], want, "bf16", 1.0, "16384-wide NV12")
+
+
+@pytest.mark.parametrize("src", ["nv12", "packed"])
+def test_reduce_pillarbox_fill_columns(F, W, src):
+    """ReduceDPP over a portrait image letterboxed into a square: spans wholly
+    in the fill columns are reduced from one chain evaluation, spans across
+    the window edge pixel by pixel; the statistics match the oracle's."""
+    ow = oh = 128
+    if src == "nv12":
+        frames = synth.nv12_frames(27, 2, 320, 180)
+        srcs = [torch.from_numpy(frames[i]).cuda() for i in range(2)]
+        layout, read = F.FKL_LAYOUT_NV12, F.read_nv12()
+        rgb = [O.nv12_to_rgb(frames[i]) for i in range(2)]
+    else:
+        imgs = [synth.packed_image(28 + i, 300, 170) for i in range(2)]
+        srcs = [torch.from_numpy(im).cuda() for im in imgs]
+        layout, read = None, F.read_u8c3()
+        rgb = [im.astype(np.float64) for im in imgs]
+    p = F.Pipeline([read, F.letterbox(ow, oh, 114.0), F.mul(W.INV255), F.write_split(F.FKL_E4M3, 1.0)])
+    out = torch.zeros((2, 3, oh, ow), dtype=torch.float8_e4m3fn, device="cuda")
+    stats = torch.zeros(32, device="cuda")
+    F.fkl_reduce_batch(p.handle, [F.as_fkl(s, layout) for s in srcs], None, F.as_fkl(out, F.FKL_LAYOUT_NCHW),
+                       stats.data_ptr())
+    torch.cuda.synchronize()
+    st = stats.cpu().numpy().astype(np.float64)
+    vals = np.stack([O.split(O.multiply(O.letterbox(rgb[i], ow, oh, 114.0), 1 / 255)) for i in range(2)])
+    want = O.reduce_stats(vals)
+    check_f32(st[0:3], want["min"], "min")
+    check_f32(st[3:6], want["max"], "max")
+    np.testing.assert_allclose(st[6:9], want["mean"], rtol=1e-6)
+    check_f32(st[9], want["amax"], "amax")
