@@ -26,7 +26,7 @@ struct Args2D {
 // minimum number of resident 256-thread blocks per SM (OccupancyBound), which
 // caps its registers: 8 pixels per thread, bf16/f16, 6 blocks (40 registers
 // instead of 48, 16 spilled bytes; +2% on 256 frames); 16 pixels per thread,
-// FP8, 4 blocks (64 instead of 78, 16-44 spilled bytes; +5%). These loads are
+// FP8, 4 blocks (64 instead of 78, 32 spilled bytes; +5%). These loads are
 // latency-bound, so more resident warps pay for the spills; under the same
 // caps the general resize and the two-row variants spilled 44-550 bytes.
 template <class RB, class W, int V, int RY>
