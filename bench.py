@@ -249,6 +249,7 @@ class VChain(Workload):
         self.sector_bytes = 8 * n
         self.oracle_spec = ("vchain", {"L": L}, 8 * (1 << 20))
         self.name = f"64M f32 uniform[-1,1], {L} alternating mul/add (FMA off), f32 out"
+        self.traffic_key = f"vchain_f32_64M_L{L}"
         self.launches_per_step = max(1, (L + 4095) // 4096)
         self.h2d_bytes = 4 * n
         self.d2h_bytes = 4 * n
