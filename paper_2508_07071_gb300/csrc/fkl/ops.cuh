@@ -737,14 +737,14 @@ struct WriteSplit {
           for (int k = 0; k < V; k += 2) f2split(f2mul(f2(v[k].v[c], v[k + 1].v[c]), inv2), run[k], run[k + 1]);
           store_run<OutT, V>(q + c * p.plane, run);
         }
-        return;
-      }
+      } else {
 #pragma unroll
-      for (int c = 0; c < C; ++c) {
-        float run[V];
+        for (int c = 0; c < C; ++c) {
+          float run[V];
 #pragma unroll
-        for (int k = 0; k < V; ++k) run[k] = prescale<OutT>(v[k].v[c], p);
-        store_run<OutT, V>(q + c * p.plane, run);
+          for (int k = 0; k < V; ++k) run[k] = prescale<OutT>(v[k].v[c], p);
+          store_run<OutT, V>(q + c * p.plane, run);
+        }
       }
     } else {
 #pragma unroll
