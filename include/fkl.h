@@ -156,9 +156,11 @@ typedef struct fkl_pipeline_s* fkl_pipeline;  /* library-owned handle        */
  *        Divide -> Write: the input is cast to the compute type -- F64 for an
  *        F64 output, else F32 -- then every op runs and rounds once in it,
  *        constants f[0] taken exactly into it; the write rounds to the output
- *        type to nearest even (E4M3: the F32 product with fl32(1/s) is rounded,
- *        saturating at +-448). A READ_F32|READ_U8 chain of MUL/ADD only
- *        writing F32 is a vertical chain)
+ *        type to nearest even (E4M3: sat_RNE(v / s), saturating at +-448;
+ *        the kernel forms v / s as the F32 product with fl32(1/s), so next to
+ *        an E4M3 tie the stored code may be the neighbour of the rounded
+ *        exact quotient, within one E4M3 ulp). A READ_F32|READ_U8 chain of
+ *        MUL/ADD only writing F32 is a vertical chain)
  * An absent MUL/ADD/SUB/DIV is bound as its identity (x*1, x-0, x/1 are
  * exact, so the result equals the shorter chain bit for bit). A chain of the
  * right grammar outside this set returns FKL_ERR_UNSUPPORTED.

@@ -325,8 +325,12 @@ def typed_chain(x: np.ndarray, out_dtype: str, mul=None, sub=None, div=None, sca
     constants are float32 values (what a descriptor carries) taken exactly
     into the compute type. An absent op is skipped. The write rounds to the
     output type: f16 and bf16 round to nearest even (returned as float64
-    values); e4m3 first multiplies by the float32 value of 1/scale (one
-    float32 rounding), then rounds to nearest even with saturation.
+    values); e4m3 stores sat_RNE(v / s): the compute value v divided by the
+    per-tensor scale s (the float32 value of `scale`) in float64, then
+    rounded to nearest even with saturation at +-448. The quotient of a
+    float32 v by a float32 s can round in float64 only far from an E4M3 tie
+    (an E4M3 tie has at most 5 significant bits, and a float64 rounding error
+    of v/s is 2^-53 relative), so this is the rounding of the exact quotient.
     """
     if out_dtype not in ("f32", "f64", "f16", "bf16", "e4m3"):
         raise ValueError("typed chains write f32, f64, f16, bf16 or e4m3")
@@ -343,8 +347,7 @@ def typed_chain(x: np.ndarray, out_dtype: str, mul=None, sub=None, div=None, sca
     if out_dtype == "f16":
         return round_f16(y)
     if out_dtype == "e4m3":
-        inv = np.float32(1.0 / float(np.float32(scale)))
-        return round_e4m3(np.multiply(y, inv, dtype=np.float32))
+        return round_e4m3(y.astype(np.float64) / float(np.float32(scale)))
     return y
 
 

@@ -3,8 +3,10 @@
 // The input element is cast to the compute type CT (float64 for a float64
 // output, float32 otherwise), then each present op runs once in CT with IEEE
 // round-to-nearest-even; absent ops are skipped (a uniform branch). The
-// write rounds to the output type (FP8: the float32 product with fl32(1/s)
-// first, then round-to-nearest-even with saturation). One thread handles E
+// write rounds to the output type (FP8: sat_RNE(v / s), with v / s formed as
+// the float32 product with fl32(1/s): next to an E4M3 tie the code may be the
+// neighbour of the rounded exact quotient, within one E4M3 ulp, and is
+// otherwise the same). One thread handles E
 // consecutive elements of one tensor; blockIdx.y is the tensor (horizontal
 // fusion).
 #pragma once
