@@ -171,7 +171,11 @@ FKL_API fkl_status fkl_pipeline_create(const fkl_op_desc* ops, int32_t n_ops,
                                fkl_pipeline* out);
 
 /*
- * Run the chain once: one image `in` to one output `out` (batch of one).
+ * Run the chain once: one image `in` to one output `out` (batch of one) --
+ * the TransformDPP of paper §IV-C over one image: every output pixel reads
+ * its value through the ROp, passes it through the COps in order and stores
+ * it with the WOp, in one kernel (vertical fusion, paper §II Fig. 3B and
+ * Algorithm 1 "KernelFunctionB").
  * Image chains: `in` is HWC u8 (READ_U8C3) or NV12 (READ_NV12); the ROI is the
  * CROP descriptor's, else the whole image. `out` is NCHW (WRITE_SPLIT) or
  * NHWC (WRITE_PACKED) with N = 1 and the dtype the WOp names; its H, W must
@@ -203,10 +207,22 @@ FKL_API fkl_status fkl_execute_batch(fkl_pipeline p, int32_t n, const fkl_tensor
                              const int32_t* rois, fkl_tensor* out,
                              void* stream);
 
-/* Release a pipeline. NULL is ignored. */
+/*
+ * Release a pipeline: the host-side counterpart of fkl_pipeline_create (the
+ * IOp description the executor of paper §IV-D holds). It frees host memory
+ * only; the pipeline owns no device memory and no stream, so work already
+ * enqueued with it is unaffected. NULL is ignored. Do not destroy a pipeline
+ * while another thread is calling into the library with it.
+ */
 FKL_API void fkl_pipeline_destroy(fkl_pipeline p);
 
-/* Message of the last failed call on this thread ("" if none). */
+/*
+ * Message of the last failed call on this thread ("" if none). The paper
+ * defines no error reporting (its C++ API fails at compile time, §IV-D); a C
+ * ABI binds chains at run time, so every call returns an fkl_status and this
+ * thread-local text says which argument or CUDA call failed. The pointer is
+ * valid until the next library call on the same thread.
+ */
 FKL_API const char* fkl_last_error(void);
 
 /* ------------------------------------------------------------------------ */

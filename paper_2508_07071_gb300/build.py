@@ -3,7 +3,8 @@
 Every translation unit under csrc/ is compiled by nvcc in parallel, then
 linked into paper_2508_07071_gb300/libfkl.so. Objects go to
 paper_2508_07071_gb300/_build/. A build is skipped when the library is newer
-than every source and header.
+than every source and header; otherwise only the objects whose source, or a
+header they include (nvcc's dependency files), changed are compiled again.
 """
 from __future__ import annotations
 
@@ -56,14 +57,42 @@ def up_to_date() -> bool:
     return all(os.path.getmtime(f) <= t for f in _all_inputs())
 
 
-def _compile(src: str, extra: list[str]) -> str:
+def _deps(dep_file: str) -> list[str] | None:
+    """Files an object was compiled from, from nvcc's dependency file (None
+    when there is none)."""
+    if not os.path.exists(dep_file):
+        return None
+    text = open(dep_file).read().replace("\\\n", " ")
+    _, _, rest = text.partition(":")
+    return [f for f in rest.split() if f]
+
+
+def _object_current(src: str, obj: str, extra: list[str]) -> bool:
+    """Whether `obj` is newer than its source, every header it included and
+    the build script, and was compiled with the same extra flags."""
+    dep, flags = obj[:-2] + ".d", obj[:-2] + ".flags"
+    deps = _deps(dep)
+    if deps is None or not os.path.exists(obj) or not os.path.exists(flags):
+        return False
+    if open(flags).read() != " ".join(extra):
+        return False
+    t = os.path.getmtime(obj)
+    return all(os.path.exists(f) and os.path.getmtime(f) <= t for f in deps + [src, os.path.abspath(__file__)])
+
+
+def _compile(src: str, extra: list[str], force: bool = False) -> str:
     obj = os.path.join(BUILD, os.path.basename(src).replace(".cu", ".o"))
-    cmd = [nvcc(), *ARCH, *NVCC_FLAGS, *extra, "-I", os.path.join(ROOT, "include"), "-c", src, "-o", obj]
+    if not force and _object_current(src, obj, extra):
+        return obj
+    cmd = [nvcc(), *ARCH, *NVCC_FLAGS, *extra, "-I", os.path.join(ROOT, "include"), "-c", src, "-o", obj,
+           "-MD", "-MF", obj[:-2] + ".d"]
     r = subprocess.run(cmd, capture_output=True, text=True)
     if r.returncode != 0:
         raise RuntimeError(f"nvcc failed on {os.path.basename(src)}:\n{r.stderr[-6000:]}")
     if r.stderr.strip():
         sys.stderr.write(r.stderr)
+    with open(obj[:-2] + ".flags", "w") as f:
+        f.write(" ".join(extra))
     return obj
 
 
@@ -78,7 +107,7 @@ def build(force: bool = False, verbose: bool = False, extra: list[str] | None = 
     srcs = sources()
     workers = min(len(srcs), os.cpu_count() or 4)
     with cf.ThreadPoolExecutor(workers) as ex:
-        objs = list(ex.map(lambda s: _compile(s, extra), srcs))
+        objs = list(ex.map(lambda s: _compile(s, extra, force), srcs))
     tmp = LIB + ".tmp"
     cmd = [nvcc(), *ARCH, "-shared", "-cudart", "shared", "-o", tmp, *objs,
            "-Xlinker", "-rpath,/usr/local/cuda/lib64"]

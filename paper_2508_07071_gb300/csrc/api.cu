@@ -19,15 +19,15 @@ namespace fkl_impl {
 
 namespace {
 
-thread_local std::string t_error;
+// The last error message of this thread: a fixed buffer, so that reporting a
+// failure never allocates.
+thread_local char t_error[512];
 
 fkl_status fail(fkl_status s, const char* fmt, ...) {
-  char buf[512];
   va_list ap;
   va_start(ap, fmt);
-  std::vsnprintf(buf, sizeof(buf), fmt, ap);
+  std::vsnprintf(t_error, sizeof(t_error), fmt, ap);
   va_end(ap);
-  t_error = buf;
   return s;
 }
 
@@ -369,7 +369,7 @@ void place(const Spec& s, int out_w, int out_h, fkl::ResampleParams& r) {
   if (r.rw == 2 * r.dw && r.rh == 2 * r.dh) r.flags |= fkl::kExact2x;
 }
 
-void set_last_error(const char* msg) { t_error = msg; }
+void set_last_error(const char* msg) { std::snprintf(t_error, sizeof(t_error), "%s", msg ? msg : ""); }
 
 int sm_count() {
   int dev = 0;
@@ -567,7 +567,7 @@ cudaError_t launch_family(const LaunchCtx& c) {
 // one length, one LINEAR output of n * length elements of the write's type
 // (tensor i at elements [i * length, (i + 1) * length)).
 fkl_status check_linear(const Spec& s, int32_t n, const fkl_tensor* ins, const int32_t* rois,
-                        const fkl_tensor* out, int64_t& len, std::vector<const void*>& ptrs) {
+                        const fkl_tensor* out, int64_t& len) {
   const int in_dt = s.family == FAM_CAST ? s.in_dtype : (s.vinput_u8 ? FKL_U8 : FKL_F32);
   const int out_dt = s.family == FAM_CAST ? s.out_dtype : FKL_F32;
   if (n < 0) return fail(FKL_ERR_INVALID, "negative batch size");
@@ -577,11 +577,6 @@ fkl_status check_linear(const Spec& s, int32_t n, const fkl_tensor* ins, const i
   if (out->layout != FKL_LAYOUT_LINEAR || out->dtype != out_dt)
     return fail(FKL_ERR_INVALID, "tensor chains need a LINEAR %s output", dtype_name(out_dt));
   len = n > 0 ? ins[0].dims[0] : 0;
-  try {
-    ptrs.resize(n);
-  } catch (...) {
-    return fail(FKL_ERR_OOM, "host allocation failed");
-  }
   for (int i = 0; i < n; ++i) {
     const fkl_tensor& t = ins[i];
     if (t.layout != FKL_LAYOUT_LINEAR || t.dtype != in_dt)
@@ -590,7 +585,6 @@ fkl_status check_linear(const Spec& s, int32_t n, const fkl_tensor* ins, const i
       return fail(FKL_ERR_INVALID, "input %d has %lld elements, input 0 has %lld", i, (long long)t.dims[0],
                   (long long)len);
     if (!t.data && len > 0) return fail(FKL_ERR_INVALID, "input %d: data is NULL", i);
-    ptrs[i] = t.data;
   }
   if (len > (int64_t(1) << 40) || out->dims[0] != int64_t(n) * len)
     return fail(FKL_ERR_INVALID, "output must hold n x length = %lld elements (has %lld)",
@@ -606,35 +600,66 @@ size_t linear_workspace_bytes(const Spec& s, int64_t len) {
   return narrow ? static_cast<size_t>((len * 4 + 255) / 256 * 256) : 0;
 }
 
-// Runs a tensor chain: typed chains in one launch per 256 tensors, vertical
-// chains one launch per tensor (and per 4096 ops); unfused: one kernel per op,
-// with `ws` (linear_workspace_bytes) when the chain needs one.
-fkl_status run_linear(fkl_pipeline p, int32_t n, const fkl_tensor* ins, const int32_t* rois, fkl_tensor* out,
+// Runs a validated tensor chain (check_linear gave `len`): typed chains in
+// one launch per 256 tensors, vertical chains one launch per tensor (and per
+// 4096 ops); unfused: one kernel per op, with `ws` (linear_workspace_bytes)
+// when the chain needs one. The input pointers travel in a stack array of
+// one launch's tensors, so the call allocates no host memory.
+constexpr int kLinearChunk = 256;  // tensors per typed-chain launch
+
+fkl_status run_linear(fkl_pipeline p, int32_t n, const fkl_tensor* ins, fkl_tensor* out, int64_t len,
                       bool unfused, void* stream, void* ws = nullptr, size_t ws_bytes = 0) {
-  int64_t len = 0;
-  std::vector<const void*> ptrs;
-  const fkl_status st = check_linear(p->spec, n, ins, rois, out, len, ptrs);
-  if (st != FKL_OK) return st;
   if (n == 0 || len == 0) return FKL_OK;
   const size_t need = unfused ? linear_workspace_bytes(p->spec, len) : 0;
   if (need && (!ws || ws_bytes < need || reinterpret_cast<uintptr_t>(ws) % 256))
     return fail(FKL_ERR_INVALID, "workspace must be >= %zu bytes and 256-byte aligned", need);
   const cudaStream_t cs = static_cast<cudaStream_t>(stream);
+  const int64_t esz = dtype_bytes(out->dtype);
+  const void* ptrs[kLinearChunk];
   cudaError_t e = cudaSuccess;
-  if (p->spec.family == FAM_CAST) {
-    e = unfused ? launch_unfused_cast(p->spec, n, ptrs.data(), out->data, len, ws, cs)
-                : launch_cast(p->spec, p->shape, n, ptrs.data(), out->data, len, cs);
-  } else {
-    for (int i = 0; i < n && e == cudaSuccess; ++i) {
-      float* o = static_cast<float*>(out->data) + i * len;
-      e = unfused ? launch_unfused_vchain(p->spec, ptrs[i], o, len, cs)
-                  : launch_vchain(p->spec, p->shape, ptrs[i], o, len, cs);
+  for (int start = 0; start < n && e == cudaSuccess; start += kLinearChunk) {
+    const int m = std::min(kLinearChunk, n - start);
+    for (int i = 0; i < m; ++i) ptrs[i] = ins[start + i].data;
+    uint8_t* o = static_cast<uint8_t*>(out->data) + start * len * esz;
+    if (p->spec.family == FAM_CAST) {
+      e = unfused ? launch_unfused_cast(p->spec, m, ptrs, o, len, ws, cs)
+                  : launch_cast(p->spec, p->shape, m, ptrs, o, len, cs);
+    } else {
+      for (int i = 0; i < m && e == cudaSuccess; ++i) {
+        float* oi = reinterpret_cast<float*>(o) + i * len;
+        e = unfused ? launch_unfused_vchain(p->spec, ptrs[i], oi, len, cs)
+                    : launch_vchain(p->spec, p->shape, ptrs[i], oi, len, cs);
+      }
     }
   }
   return e == cudaSuccess ? FKL_OK : cuda_fail(e, unfused ? "unfused launch" : "tensor chain launch");
 }
 
+// check_linear, then run_linear.
+fkl_status exec_linear(fkl_pipeline p, int32_t n, const fkl_tensor* ins, const int32_t* rois, fkl_tensor* out,
+                       bool unfused, void* stream, void* ws = nullptr, size_t ws_bytes = 0) {
+  int64_t len = 0;
+  const fkl_status st = check_linear(p->spec, n, ins, rois, out, len);
+  if (st != FKL_OK) return st;
+  return run_linear(p, n, ins, out, len, unfused, stream, ws, ws_bytes);
+}
+
 bool is_tensor_chain(const Spec& s) { return s.family == FAM_VCHAIN || s.family == FAM_CAST; }
+
+// Sizing of the unfused image chains' intermediates, shared by every unfused
+// entry point: each intermediate holds one image's pixels, packed (3 bytes
+// per pixel in the integer chains, 3 float32 otherwise), at the output size,
+// or for NV12 chains at least the source window (the decode runs at full
+// resolution); slots are rounded up to 256 bytes.
+int64_t unfused_min_px(const OutDesc& od) { return static_cast<int64_t>(od.H) * od.W; }
+int64_t unfused_image_px(const Spec& s, const OutDesc& od, const fkl::ResampleParams& r) {
+  const int64_t px = unfused_min_px(od);
+  return s.family == FAM_NV12 ? std::max<int64_t>(px, static_cast<int64_t>(r.rw) * r.rh) : px;
+}
+int64_t unfused_slot_bytes(const Spec& s, int64_t px) {
+  const int64_t elem = s.family == FAM_INT ? 3 : 12;
+  return (px * elem + 255) / 256 * 256;
+}
 
 fkl_status validate_batch(const fkl_pipeline p, int32_t n, const fkl_tensor* ins, const int32_t* rois,
                           const fkl_tensor* out, OutDesc& od, std::vector<fkl::ResampleParams>& imgs) {
@@ -663,7 +688,7 @@ namespace {
 // fkl_execute_batch with an optional device-side FP8 scale.
 fkl_status execute_batch_impl(fkl_pipeline p, int32_t n, const fkl_tensor* ins, const int32_t* rois,
                               fkl_tensor* out, const float* scale_inv_dev, void* stream) {
-  if (p && is_tensor_chain(p->spec)) return run_linear(p, n, ins, rois, out, false, stream);
+  if (p && is_tensor_chain(p->spec)) return exec_linear(p, n, ins, rois, out, false, stream);
   OutDesc od;
   std::vector<fkl::ResampleParams> imgs;
   fkl_status st = validate_batch(p, n, ins, rois, out, od, imgs);
@@ -721,7 +746,7 @@ fkl_status fkl_pipeline_create(const fkl_op_desc* ops, int32_t n_ops, fkl_pipeli
 
 void fkl_pipeline_destroy(fkl_pipeline p) { delete p; }
 
-const char* fkl_last_error(void) { return t_error.c_str(); }
+const char* fkl_last_error(void) { return t_error; }
 
 fkl_status fkl_set_device_wait_limit(uint64_t ns) {
   if (ns > kMaxWaitNs) return fail(FKL_ERR_INVALID, "wait limit above 10 s");
@@ -842,8 +867,7 @@ fkl_status fkl_unfused_workspace_bytes(fkl_pipeline p, int32_t n, const fkl_tens
   if (!p) return fail(FKL_ERR_INVALID, "null pipeline");
   if (is_tensor_chain(p->spec)) {
     int64_t len = 0;
-    std::vector<const void*> ptrs;
-    const fkl_status st = check_linear(p->spec, n, ins, rois, out, len, ptrs);
+    const fkl_status st = check_linear(p->spec, n, ins, rois, out, len);
     if (st != FKL_OK) return st;
     *bytes = linear_workspace_bytes(p->spec, len);
     return FKL_OK;
@@ -852,12 +876,9 @@ fkl_status fkl_unfused_workspace_bytes(fkl_pipeline p, int32_t n, const fkl_tens
   std::vector<fkl::ResampleParams> imgs;
   const fkl_status st = validate_batch(p, n, ins, rois, out, od, imgs);
   if (st != FKL_OK) return st;
-  const int64_t elem = p->spec.family == FAM_INT ? 3 : 12;
-  int64_t need = static_cast<int64_t>(od.H) * od.W;
-  if (p->spec.family == FAM_NV12)
-    for (const auto& r : imgs) need = std::max<int64_t>(need, static_cast<int64_t>(r.rw) * r.rh);
-  const int64_t each = (need * elem + 255) / 256 * 256;
-  *bytes = static_cast<size_t>(2 * each);
+  int64_t px = 0;
+  for (const auto& r : imgs) px = std::max(px, unfused_image_px(p->spec, od, r));
+  *bytes = static_cast<size_t>(2 * unfused_slot_bytes(p->spec, std::max(px, unfused_min_px(od))));
   return FKL_OK;
 }
 
@@ -865,7 +886,7 @@ fkl_status fkl_execute_batch_unfused(fkl_pipeline p, int32_t n, const fkl_tensor
                                      fkl_tensor* out, void* workspace, size_t workspace_bytes, void* stream) {
   if (!p) return fail(FKL_ERR_INVALID, "null pipeline");
   const cudaStream_t s = static_cast<cudaStream_t>(stream);
-  if (is_tensor_chain(p->spec)) return run_linear(p, n, ins, rois, out, true, stream, workspace, workspace_bytes);
+  if (is_tensor_chain(p->spec)) return exec_linear(p, n, ins, rois, out, true, stream, workspace, workspace_bytes);
   size_t need = 0;
   fkl_status st = fkl_unfused_workspace_bytes(p, n, ins, rois, out, &need);
   if (st != FKL_OK) return st;
@@ -876,7 +897,7 @@ fkl_status fkl_execute_batch_unfused(fkl_pipeline p, int32_t n, const fkl_tensor
   st = validate_batch(p, n, ins, rois, out, od, imgs);
   if (st != FKL_OK) return st;
   uint8_t* ws0 = static_cast<uint8_t*>(workspace);
-  uint8_t* ws1 = ws0 + need / 2;
+  uint8_t* ws1 = ws0 + need / 2;  // need = 2 x unfused_slot_bytes
   for (int i = 0; i < n; ++i) {
     const cudaError_t e = launch_unfused_image(p->spec, imgs[i], od.p, i, od.H, od.W, ws0, ws1, s);
     if (e != cudaSuccess) return cuda_fail(e, "unfused launch");
@@ -1016,15 +1037,20 @@ fkl_status fkl_execute_batch_unfused_static(fkl_pipeline p, int32_t n, const fkl
   const cudaStream_t s = static_cast<cudaStream_t>(stream);
   if (is_tensor_chain(p->spec)) {  // the float32 copy of one tensor, if any, lives in the static scratch
     int64_t len = 0;
-    std::vector<const void*> ptrs;
-    const fkl_status st = check_linear(p->spec, n, ins, rois, out, len, ptrs);
+    const fkl_status st = check_linear(p->spec, n, ins, rois, out, len);
     if (st != FKL_OK) return st;
+    const size_t need = linear_workspace_bytes(p->spec, len);
+    if (need > kStaticScratchBytes)
+      return fail(FKL_ERR_INVALID,
+                  "tensors of %lld elements need %zu bytes of scratch; the static scratch holds %zu bytes "
+                  "(use fkl_execute_batch_unfused with a caller workspace)",
+                  static_cast<long long>(len), need, kStaticScratchBytes);
     void* scratch = nullptr;
-    if (linear_workspace_bytes(p->spec, len) > 0) {
+    if (need > 0 && n > 0) {
       const cudaError_t e = static_scratch(&scratch);
       if (e != cudaSuccess) return cuda_fail(e, "static scratch lookup");
     }
-    return run_linear(p, n, ins, rois, out, true, stream, scratch, kStaticScratchBytes);
+    return run_linear(p, n, ins, out, len, true, stream, scratch, kStaticScratchBytes);
   }
   if (n < 0) return fail(FKL_ERR_INVALID, "negative batch size");
   if (n > 0 && !ins) return fail(FKL_ERR_INVALID, "inputs missing");
@@ -1033,15 +1059,14 @@ fkl_status fkl_execute_batch_unfused_static(fkl_pipeline p, int32_t n, const fkl
   if (st != FKL_OK) return st;
   // First pass: validate every image and size the two intermediates (no
   // host or device allocation: one image's parameters at a time).
-  const int64_t elem = p->spec.family == FAM_INT ? 3 : 12;
-  int64_t px = static_cast<int64_t>(od.H) * od.W;
+  int64_t px = unfused_min_px(od);
   for (int i = 0; i < n; ++i) {
     fkl::ResampleParams r;
     st = image_params(p->spec, &ins[i], rois, i, od, r);
     if (st != FKL_OK) return st;
-    if (p->spec.family == FAM_NV12) px = std::max<int64_t>(px, static_cast<int64_t>(r.rw) * r.rh);
+    px = std::max(px, unfused_image_px(p->spec, od, r));
   }
-  const int64_t each = (px * elem + 255) / 256 * 256;
+  const int64_t each = unfused_slot_bytes(p->spec, px);
   if (2 * each > static_cast<int64_t>(kStaticScratchBytes))
     return fail(FKL_ERR_INVALID,
                 "these images need %lld bytes of scratch; the static scratch holds %zu bytes "

@@ -27,8 +27,8 @@ TRAFFIC = os.path.join(ROOT, "profiles", "traffic.json")
 
 def source_hash(files: list[str] | None = None) -> str:
     """Hash of the CUDA sources a kernel is compiled from (paths relative to
-    csrc/; all of them when `files` is None) and of the build script (its
-    flags change the kernels as much as sources do)."""
+    csrc/; all of them when `files` is None) and of the build flags (they
+    change the kernels as much as sources do)."""
     h = hashlib.sha256()
     base = os.path.join(PKG, "csrc")
     if files is None:
@@ -38,8 +38,8 @@ def source_hash(files: list[str] | None = None) -> str:
         h.update(rel.encode())
         with open(os.path.join(base, rel), "rb") as fh:
             h.update(fh.read())
-    with open(os.path.join(PKG, "build.py"), "rb") as fh:
-        h.update(fh.read())
+    from . import build
+    h.update(" ".join(build.ARCH + build.NVCC_FLAGS).encode())
     return h.hexdigest()[:16]
 
 

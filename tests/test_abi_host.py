@@ -297,3 +297,46 @@ def test_static_unfused_validates_tensor_chains_before_any_device_call(F):
         assert ei.value.status == F.FKL_ERR_INVALID
     finally:
         F.fkl_pipeline_destroy(p)
+
+
+def test_static_unfused_refuses_tensors_beyond_its_scratch_before_any_device_call(F):
+    """A typed chain writing bf16 keeps one tensor's float32 values in the
+    static scratch (32 MiB): 9M elements (36 MB) are refused on the host with
+    a message about that scratch, before the scratch's address is looked up."""
+    from paper_2508_07071_gb300 import workloads as W
+    p = F.fkl_pipeline_create(W.typed_chain(F.FKL_F32, F.FKL_BF16, 2.0))
+    try:
+        n = 9 * 2**20
+        a = F._tensor(0x1000, (n,), 0, F.FKL_F32, F.FKL_LAYOUT_LINEAR)
+        o = F._tensor(0x9000, (n,), 0, F.FKL_BF16, F.FKL_LAYOUT_LINEAR)
+        with pytest.raises(F.FklError) as ei:
+            F.fkl_execute_batch_unfused_static(p, [a], None, o, stream=0)
+        assert ei.value.status == F.FKL_ERR_INVALID
+        assert "static scratch" in str(ei.value)
+        # the caller-workspace form reports what it would need instead
+        assert F.fkl_unfused_workspace_bytes(p, [a], None, o) == n * 4
+    finally:
+        F.fkl_pipeline_destroy(p)
+
+
+def test_error_messages_are_kept_per_thread_and_truncated(F):
+    """fkl_last_error is thread-local text in a fixed buffer (reporting a
+    failure allocates nothing); a long message is cut, not overflowed."""
+    import threading
+    from paper_2508_07071_gb300 import workloads as W
+    p = F.fkl_pipeline_create(W.typed_chain(F.FKL_F32, F.FKL_BF16, 2.0))
+    try:
+        a = F._tensor(0x1000, (10,), 0, F.FKL_F32, F.FKL_LAYOUT_LINEAR)
+        o = F._tensor(0x9000, (11,), 0, F.FKL_BF16, F.FKL_LAYOUT_LINEAR)
+        with pytest.raises(F.FklError):
+            F.fkl_execute_batch(p, [a], None, o, stream=0)
+        here = F._lib.fkl_last_error().decode()
+        assert "output must hold" in here and len(here) < 512
+        seen = []
+        t = threading.Thread(target=lambda: seen.append(F._lib.fkl_last_error().decode()))
+        t.start()
+        t.join()
+        assert seen == [""]
+        assert F._lib.fkl_last_error().decode() == here
+    finally:
+        F.fkl_pipeline_destroy(p)
