@@ -107,6 +107,14 @@ class NV12Letterbox(Workload):
         self.F.fkl_execute_batch_unfused(self.pipe.handle, self.ins, None, self.o,
                                          self.ws.data_ptr(), self.ws_bytes, stream=stream)
 
+    def step_per_op(self, stream, timed=False):
+        if getattr(self, "ws_op", None) is None:
+            nb = self.F.fkl_per_op_workspace_bytes(self.pipe.handle, self.ins, None, self.o)
+            self.ws_op = self.torch.empty(nb, dtype=self.torch.uint8, device="cuda")
+            self.ws_op_bytes = nb
+        return self.F.fkl_execute_batch_per_op(self.pipe.handle, self.ins, None, self.o, self.ws_op.data_ptr(),
+                                               self.ws_op_bytes, stream=stream, timed=timed)
+
     def unfused_bytes(self):
         # decode (read NV12, write f32 RGB), letterbox (read taps, write f32),
         # x1/255 (read + write f32), split+cast (read f32, write out)
@@ -204,6 +212,14 @@ class PackedBatch(Workload):
             self.ws_bytes = nb
         self.F.fkl_execute_batch_unfused(self.pipe.handle, self.ins, self.rois, self.o,
                                          self.ws.data_ptr(), self.ws_bytes, stream=stream)
+
+    def step_per_op(self, stream, timed=False):
+        if getattr(self, "ws_op", None) is None:
+            nb = self.F.fkl_per_op_workspace_bytes(self.pipe.handle, self.ins, self.rois, self.o)
+            self.ws_op = self.torch.empty(nb, dtype=self.torch.uint8, device="cuda")
+            self.ws_op_bytes = nb
+        return self.F.fkl_execute_batch_per_op(self.pipe.handle, self.ins, self.rois, self.o, self.ws_op.data_ptr(),
+                                               self.ws_op_bytes, stream=stream, timed=timed)
 
     def between_steps(self):
         self.flush.fill_(1)
@@ -329,6 +345,123 @@ def time_steps_queued(torch, fn, K, stream):
     return time_steps(torch, fn, K, stream)
 
 
+def measure_unfused(torch, wl, steps, stream, between, fused_ms, peak):
+    """The unfused chain on the same GPU in both forms: one kernel per op over
+    the whole batch (the paper's unfused chain, per-kernel GB/s from a timed
+    call) and one kernel per op and image (the horizontal-fusion comparison),
+    each also replayed as a captured CUDA graph."""
+    out = {"traffic_ratio": round(wl.unfused_bytes() / wl.bytes, 2), "steps": steps}
+
+    def timed(fn):
+        fn(stream)
+        torch.cuda.synchronize()
+        ms = float(np.mean(time_steps(torch, fn, steps, stream, between)))
+        graph = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(graph, stream=stream):
+            fn(stream)
+        graph.replay()
+        torch.cuda.synchronize()
+        gms = float(np.mean(time_steps(torch, lambda st: graph.replay(), steps, stream, between)))
+        return {"ms_per_step": round(ms, 4), "speedup": round(ms / fused_ms, 2),
+                "cuda_graph_ms_per_step": round(gms, 4), "speedup_vs_cuda_graph": round(gms / fused_ms, 2)}
+
+    if hasattr(wl, "step_per_op"):
+        d = timed(wl.step_per_op)
+        if between:
+            between()
+        rep = wl.step_per_op(stream, timed=True)  # one call with events around every kernel
+        d["kernels"] = [{"name": name, "launches": int(k), "ms": round(ms, 4),
+                         "GBps": round(b / (ms * 1e-3) / 1e9, 1) if ms > 0 else None,
+                         "frac": round(b / (ms * 1e-3) / 1e9 / peak, 4) if ms > 0 else None}
+                        for name, k, b, ms in rep]
+        d["launches_per_step"] = int(sum(k for _, k, _, _ in rep))
+        d["form"] = "one kernel per op over the batch (fkl_execute_batch_per_op)"
+        out["per_op"] = d
+        d = timed(wl.step_unfused)
+        d["form"] = "one kernel per op and image (fkl_execute_batch_unfused)"
+        out["per_image"] = d
+    else:  # tensor chains: the unfused form is already one kernel per op over the tensor
+        d = timed(wl.step_unfused)
+        d["form"] = "one kernel per op over the tensor (fkl_execute_batch_unfused)"
+        d["launches_per_step"] = int(max(1, wl.L))
+        d["kernel_GBps"] = round(wl.bytes / (d["ms_per_step"] / max(1, wl.L) * 1e-3) / 1e9, 1)
+        d["kernel_frac"] = round(d["kernel_GBps"] / peak, 4)
+        out["per_op"] = d
+    return out
+
+
+def roofline_of(torch, wl, kernel_ms, peak, peak_kind, clocks, local):
+    achieved = wl.bytes / wl.launches_per_step / (kernel_ms * 1e-3) / 1e9
+    roofline = {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
+                "frac": round(achieved / peak, 4),
+                "traffic": measured_traffic(getattr(wl, "traffic_key", "")),
+                "peak_source": f"{peak_kind} copy bandwidth (MEASURED_PEAKS.json hbm_gbs)"
+                if peak_kind == "measured" else "fallback 6.8 TB/s",
+                "frac_of_8tbs": round(achieved / 8000.0, 4)}
+    if getattr(wl, "alu_ops", 0):
+        # FP32 ALU roofline: SMs x 128 FP32 lanes x the maximum SM clock, one
+        # op per lane and clock; the bound is whichever of the two takes longer
+        sms = torch.cuda.get_device_properties(local).multi_processor_count
+        mhz = clocks.get("sm_max_mhz") or 2070.0
+        alu_peak = sms * 128 * mhz * 1e6 / 1e12
+        alu_achieved = wl.alu_ops / wl.launches_per_step / (kernel_ms * 1e-3) / 1e12
+        if wl.alu_ops / (alu_peak * 1e12) > wl.bytes / (peak * 1e9):
+            roofline = {"bound": "alu", "achieved": round(alu_achieved, 2), "peak": round(alu_peak, 2),
+                        "unit": "Top/s", "frac": round(alu_achieved / alu_peak, 4), "traffic": None,
+                        "peak_source": f"{sms} SMs x 128 FP32 lanes x {mhz:.0f} MHz (max SM clock)",
+                        "hbm_frac": round(achieved / peak, 4)}
+    return roofline
+
+
+def autotune(F, wl, args, stream, between):
+    ins = wl.ins if hasattr(wl, "ins") else [wl.i]
+    rois = getattr(wl, "rois", None)
+    best, us = F.fkl_pipeline_autotune(wl.pipe.handle, ins, rois, wl.o, stream=stream,
+                                       reps=args.autotune_reps, before=between)
+    return {"shape": list(best), "us_per_launch": round(us, 2),
+            "candidates": len(F.fkl_pipeline_shapes(wl.pipe.handle))}
+
+
+def secondary_configs(args, F, W, synth, metrics, torch, stream, peak, peak_kind, clocks, local):
+    """The other workloads, measured in the same run: fused and unfused time
+    and the roofline of the fused kernel (timed after the main workload)."""
+    specs = [("single_image_224_f32", lambda: PackedBatch(F, W, synth, metrics, torch, single=True)),
+             ("hf_50_crops_128x64_f32", lambda: PackedBatch(F, W, synth, metrics, torch, single=False)),
+             ("vchain_64M_L10", lambda: VChain(F, W, synth, metrics, torch, 10)),
+             ("vchain_64M_L1000", lambda: VChain(F, W, synth, metrics, torch, 1000)),
+             ("nv12_256_letterbox_fp8", lambda: NV12Letterbox(F, W, synth, metrics, torch, args.frames, "e4m3")),
+             ("nv12_256_letterbox_f16", lambda: NV12Letterbox(F, W, synth, metrics, torch, args.frames, "f16"))]
+    out = {}
+    for key, make in specs:
+        wl = make()
+        between = getattr(wl, "between_steps", None)
+        with torch.cuda.stream(stream):
+            tuned = autotune(F, wl, args, stream, between)
+            for _ in range(3):
+                wl.step(stream)
+            torch.cuda.synchronize()
+            k = args.secondary_steps
+            times = time_steps(torch, wl.step, k, stream, between)
+            ms = float(np.mean(times))
+            kernel_ms = ms / wl.launches_per_step
+            warm_ms = None
+            if between is not None:
+                warm_ms = float(np.mean(time_steps_queued(torch, wl.step, k, stream)))
+            unf = measure_unfused(torch, wl, min(k, 3 if getattr(wl, "L", 0) >= 1000 else 5), stream, between,
+                                  ms, peak)
+        out[key] = {"workload": wl.name, "ms_per_step": round(ms, 5),
+                    "value": round(wl.bytes / (ms * 1e-3) / 1e9, 1), "unit": "GB/s",
+                    "algorithmic_bytes_per_step": int(wl.bytes), "steps": k,
+                    "warm_ms_per_step": None if warm_ms is None else round(warm_ms, 5),
+                    "roofline": roofline_of(torch, wl, kernel_ms, peak, peak_kind, clocks, local),
+                    "unfused": unf, "autotune": tuned, "kernel": F.fkl_pipeline_kernel_name(wl.pipe.handle)}
+        print(json.dumps({"secondary": key, "ms": out[key]["ms_per_step"],
+                          "frac": out[key]["roofline"]["frac"]}), file=sys.stderr, flush=True)
+        del wl
+        torch.cuda.empty_cache()
+    return out
+
+
 def run_ours(args):
     import torch
     import torch.distributed as dist
@@ -347,16 +480,12 @@ def run_ours(args):
     stream = torch.cuda.Stream()
     between = getattr(wl, "between_steps", None)
     tuned = None
+    peak, peak_kind = measured_peaks()
     with torch.cuda.stream(stream):
         if args.shape:
             F.fkl_pipeline_set_shape(wl.pipe.handle, [int(v) for v in args.shape.split(",")])
         elif not args.no_autotune:
-            ins = wl.ins if hasattr(wl, "ins") else [wl.i]
-            rois = getattr(wl, "rois", None)
-            best, us = F.fkl_pipeline_autotune(wl.pipe.handle, ins, rois, wl.o, stream=stream,
-                                               reps=args.autotune_reps, before=between)
-            tuned = {"shape": list(best), "us_per_launch": round(us, 2),
-                     "candidates": len(F.fkl_pipeline_shapes(wl.pipe.handle))}
+            tuned = autotune(F, wl, args, stream, between)
         for _ in range(args.warmup):
             wl.step(stream)
         torch.cuda.synchronize()
@@ -380,19 +509,7 @@ def run_ours(args):
 
         # unfused chain on the same GPU (a few steps)
         ku = min(args.steps, args.unfused_steps)
-        unfused_ms = graph_ms = None
-        if ku > 0:
-            wl.step_unfused(stream)
-            torch.cuda.synchronize()
-            unfused_ms = float(np.mean(time_steps(torch, wl.step_unfused, ku, stream, between)))
-            # the same per-op launches captured once in a CUDA graph and replayed
-            # (the paper's CUDA-Graphs comparison: one node per kernel)
-            graph = torch.cuda.CUDAGraph()
-            with torch.cuda.graph(graph, stream=stream):
-                wl.step_unfused(stream)
-            graph.replay()
-            torch.cuda.synchronize()
-            graph_ms = float(np.mean(time_steps(torch, lambda st: graph.replay(), ku, stream, between)))
+        unfused = measure_unfused(torch, wl, ku, stream, between, ms_per_step, peak) if ku > 0 else None
 
         # end to end through the public call with host buffers
         ke = min(args.steps, args.e2e_steps)
@@ -415,28 +532,17 @@ def run_ours(args):
                 wl.link_copy(stream)
                 link_ms = float(np.mean(time_steps(torch, wl.link_copy, ke, stream)))
 
-    peak, peak_kind = measured_peaks()
     value = total_bytes / (ms_per_step * 1e-3) / 1e9
-    achieved = wl.bytes / wl.launches_per_step / (kernel_ms * 1e-3) / 1e9
     clocks = sampler.summary()
-    roofline = {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
-                "frac": round(achieved / peak, 4),
-                "traffic": measured_traffic(getattr(wl, "traffic_key", "")),
-                "peak_source": f"{peak_kind} copy bandwidth (MEASURED_PEAKS.json hbm_gbs)"
-                if peak_kind == "measured" else "fallback 6.8 TB/s",
-                "frac_of_8tbs": round(achieved / 8000.0, 4)}
-    if getattr(wl, "alu_ops", 0):
-        # FP32 ALU roofline: SMs x 128 FP32 lanes x the maximum SM clock, one
-        # op per lane and clock; the bound is whichever of the two takes longer
-        sms = torch.cuda.get_device_properties(local).multi_processor_count
-        mhz = clocks.get("sm_max_mhz") or 2070.0
-        alu_peak = sms * 128 * mhz * 1e6 / 1e12
-        alu_achieved = wl.alu_ops / wl.launches_per_step / (kernel_ms * 1e-3) / 1e12
-        if wl.alu_ops / (alu_peak * 1e12) > wl.bytes / (peak * 1e9):
-            roofline = {"bound": "alu", "achieved": round(alu_achieved, 2), "peak": round(alu_peak, 2),
-                        "unit": "Top/s", "frac": round(alu_achieved / alu_peak, 4), "traffic": None,
-                        "peak_source": f"{sms} SMs x 128 FP32 lanes x {mhz:.0f} MHz (max SM clock)",
-                        "hbm_frac": round(achieved / peak, 4)}
+    roofline = roofline_of(torch, wl, kernel_ms, peak, peak_kind, clocks, local)
+    secondary = None
+    if rank == 0 and args.secondary and args.workload == "nv12":
+        main_name = wl.name
+        launches_main = int(args.steps * wl.launches_per_step)
+        wl_keep = wl
+        secondary = secondary_configs(args, F, W, synth, metrics, torch, stream, peak, peak_kind, clocks, local)
+        wl = wl_keep
+        assert wl.name == main_name and launches_main == int(args.steps * wl.launches_per_step)
     line = {
         "metric": METRIC,
         "value": round(value, 1),
@@ -459,11 +565,7 @@ def run_ours(args):
                    "parallelism": f"replicas x{world}", "launch_shape": list(F.fkl_pipeline_get_shape(wl.pipe.handle))
                    if hasattr(wl, "pipe") else None,
                    "kernel": F.fkl_pipeline_kernel_name(wl.pipe.handle), "autotune": tuned},
-        "unfused": None if unfused_ms is None else {
-            "ms_per_step": round(unfused_ms, 4), "speedup": round(unfused_ms / ms_per_step, 2),
-            "traffic_ratio": round(wl.unfused_bytes() / wl.bytes, 2), "steps": ku,
-            "cuda_graph_ms_per_step": round(graph_ms, 4),
-            "speedup_vs_cuda_graph": round(graph_ms / ms_per_step, 2)},
+        "unfused": unfused,
         "roofline": roofline,
         "e2e": None if e2e_ms is None else {
             "value": round(wl.bytes * world / (e2e_ms * 1e-3) / 1e9, 1), "unit": "GB/s",
@@ -476,6 +578,7 @@ def run_ours(args):
         "gpu_launches": int(args.steps * wl.launches_per_step),
         "clocks": clocks,
         "wall_s_timed": round(wall, 4),
+        "configs": secondary,
     }
     if rank == 0 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(wl, args)
@@ -892,6 +995,10 @@ def main():
     ap.add_argument("--frames", type=int, default=256)
     ap.add_argument("--chain-len", type=int, default=10)
     ap.add_argument("--unfused-steps", type=int, default=5)
+    ap.add_argument("--secondary", action=argparse.BooleanOptionalAction, default=True,
+                    help="nv12: also measure the other workloads (single image, crop batch, vertical chain "
+                         "L=10/1000, FP8 and f16 outputs) into the line's `configs`")
+    ap.add_argument("--secondary-steps", type=int, default=20)
     ap.add_argument("--e2e-steps", type=int, default=10)
     ap.add_argument("--cpu-seconds", type=float, default=10.0)
     ap.add_argument("--no-cpu-parallel", action="store_true",

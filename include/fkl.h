@@ -257,6 +257,56 @@ FKL_API fkl_status fkl_execute_batch_unfused(fkl_pipeline p, int32_t n,
                                      size_t workspace_bytes, void* stream);
 
 /*
+ * The per-op form over the whole batch: the unfused chain as the paper
+ * states it (paper §II Fig. 3A, Algorithm 1 "MainFunctionA"; the vertical-
+ * fusion comparison of §VI-B): each operation is ONE kernel over every image
+ * of a chunk, every intermediate written to and read back from device
+ * memory. fkl_execute_batch_unfused above is the per-image form (one kernel
+ * per operation and image, the horizontal-fusion comparison of §VI-C).
+ * Float image chains (READ_U8C3 / READ_NV12 families) only; others are
+ * FKL_ERR_UNSUPPORTED. The kernels run the same Operation code as the fused
+ * kernel, so the results equal fkl_execute_batch's bit for bit.
+ *
+ * Kernels, each over the chunk: NV12 chains decode the source windows to
+ * float32 RGB at full resolution (one launch per run of images with equal
+ * windows), then resize / letterbox them; packed chains crop + resize the u8
+ * source to float32 RGB; then one kernel per COp (SWAP_RB, MUL, ADD/SUB,
+ * DIV) over the chunk's pixels; then the write (split and cast).
+ * Intermediates are packed float32 images (12 bytes per pixel) in two sets
+ * of slots: an output-size slot = H x W x 12 bytes, and an input slot = (the
+ * largest of H x W and, for NV12, the source windows' w x h) x 12 bytes, both
+ * rounded up to a multiple of 768; the COp kernels ping-pong between the two
+ * sets over the chunk's output-size images only.
+ *
+ * chunk: images per launch, 1..256 (<= 0: min(n, 256)); n images run as
+ * ceil(n / chunk) rounds of every kernel.
+ * fkl_per_op_workspace_bytes: min(chunk, n) x (input slot + output slot)
+ * bytes of device workspace.
+ * fkl_execute_batch_per_op: `workspace` is caller-owned device memory of at
+ * least that size, 256-byte aligned. times (optional, NULL = none): when
+ * given, every launch is bracketed by CUDA events, the call synchronizes
+ * `stream` before it returns, and times[0 .. *n_times - 1] receive one entry
+ * per operation in chain order (at most max_times): its name, launches,
+ * algorithmic bytes read and written (the distinct tap bytes of a resize,
+ * the whole images otherwise), and device time. Without `times` the call is
+ * asynchronous and may be captured in a CUDA graph.
+ */
+typedef struct {
+  char name[32];      /* the operation, e.g. "decode NV12 -> RGB f32"          */
+  int32_t launches;   /* kernel launches of this operation in the call         */
+  double bytes;       /* algorithmic bytes its launches read and write         */
+  double ms;          /* their device time (CUDA events on the stream)         */
+} fkl_kernel_time;
+
+FKL_API fkl_status fkl_per_op_workspace_bytes(fkl_pipeline p, int32_t n, const fkl_tensor* ins,
+                                              const int32_t* rois, const fkl_tensor* out, int32_t chunk,
+                                              size_t* bytes);
+FKL_API fkl_status fkl_execute_batch_per_op(fkl_pipeline p, int32_t n, const fkl_tensor* ins, const int32_t* rois,
+                                            fkl_tensor* out, int32_t chunk, void* workspace,
+                                            size_t workspace_bytes, void* stream, fkl_kernel_time* times,
+                                            int32_t max_times, int32_t* n_times);
+
+/*
  * fkl_execute_batch_unfused_static: the unfused form above, for callers that
  * cannot allocate device memory -- for example a host framework that owns
  * every device allocation under a fixed memory budget, or a latency-critical
@@ -288,22 +338,33 @@ FKL_API fkl_status fkl_execute_batch_unfused_static(fkl_pipeline p, int32_t n, c
 /* ------------------------------------------------------------------------ */
 
 /*
- * The reduction pattern of paper §IV-C: the pipeline's ROp and COps are
- * evaluated once per output pixel of an fkl_execute_batch call with these
- * arguments, and instead of the WOp the values feed several reductions at
- * once. `out` fixes the output size and is not written. `stats` is device
- * memory of FKL_REDUCE_STATS_BYTES bytes, 16-byte aligned; when the work is
- * done (stream order) it holds floats:
+ * The reduction pattern of paper §IV-C: the statistics of the values the
+ * pipeline's chain gives every output pixel of an fkl_execute_batch call with
+ * these arguments, from one read of the inputs and with no output written.
+ * `out` fixes the output size and is not written. `stats` is device memory
+ * of FKL_REDUCE_STATS_BYTES bytes, 16-byte aligned; when the work is done
+ * (stream order) it holds floats:
  *   [0..2] minimum per channel   [3..5] maximum per channel
  *   [6..8] mean per channel      [9]    maximum absolute value, amax
  *   [10]   s = amax / 448, the per-tensor scale that maps the values onto
  *          the FP8-E4M3 range (1 when amax is 0)   [11] 1 / s
+ * and two int32 words describing the work split: [12] reduction jobs (tiles
+ * of window pixels), [13] blocks of the largest reduction launch (a
+ * persistent grid: each block walks every grid-th job).
  * Bytes 64..127 are the accumulator (overwritten). Float image families
- * only (READ_U8C3 / READ_NV12 with a resize or letterbox). Launches: two
- * memsets, one reduction launch per 256 images and one finishing kernel.
- * Min/max are exact; the mean is accumulated in 64-bit fixed point
- * (2^-20), independent of the order in which blocks finish. An empty batch
- * (n = 0) leaves NaN extremes, mean 0, amax 0 and s = 1.
+ * only (READ_U8C3 / READ_NV12 with a resize or letterbox).
+ * How: the ROp is evaluated once per pixel of each image's placed window and
+ * its per-channel extremes and sum are reduced; the COps of these chains
+ * (SWAP_RB, MUL, ADD/SUB, DIV by per-channel constants, each rounded) are
+ * monotone and affine on every channel, so the finishing kernel maps the
+ * read values' extremes through them (the result equals the extremes of
+ * the values fkl_execute_batch writes with an F32 output, bit for bit) and
+ * the mean through the affine map in float64; fill pixels (the letterbox
+ * pad) join on the host's count. Min/max are exact; sums are accumulated in
+ * 64-bit fixed point (2^-20 read units), independent of the grid and of the
+ * order in which blocks finish. Launches: two memsets, one reduction launch
+ * per 256 images and one finishing kernel. An empty batch (n = 0) leaves NaN
+ * extremes, mean 0, amax 0 and s = 1.
  */
 #define FKL_REDUCE_STATS_BYTES 128
 FKL_API fkl_status fkl_reduce_batch(fkl_pipeline p, int32_t n, const fkl_tensor* ins, const int32_t* rois,

@@ -837,6 +837,9 @@ fkl_status fkl_reduce_batch(fkl_pipeline p, int32_t n, const fkl_tensor* ins, co
   static_assert(sizeof(fkl::ReduceAcc) <= 64, "accumulator fits the stats buffer");
   cudaError_t e = cudaMemsetAsync(acc, 0, sizeof(fkl::ReduceAcc), s);
   if (e == cudaSuccess) e = cudaMemsetAsync(acc->min_key, 0xFF, sizeof(acc->min_key), s);
+  ReduceLaunch info;
+  double fill = 0.0;  // output pixels outside the placed windows: the pad value
+  for (const auto& r : imgs) fill += static_cast<double>(od.H) * od.W - static_cast<double>(r.dw) * r.dh;
   for (int start = 0; start < n && e == cudaSuccess; start += kBatchCap) {
     LaunchCtx c;
     c.spec = &p->spec;
@@ -849,9 +852,10 @@ fkl_status fkl_reduce_batch(fkl_pipeline p, int32_t n, const fkl_tensor* ins, co
     c.stream = s;
     c.all_exact2x = true;
     for (int i = 0; i < c.n; ++i) c.all_exact2x = c.all_exact2x && (c.imgs[i].flags & fkl::kExact2x);
-    e = launch_reduce(c, acc);
+    e = launch_reduce(c, acc, info);
   }
-  if (e == cudaSuccess) e = finalize_reduce(acc, static_cast<double>(n) * od.H * od.W, stats, s);
+  if (e == cudaSuccess)
+    e = finalize_reduce(p->spec, acc, static_cast<double>(n) * od.H * od.W, fill, info, stats, s);
   return e == cudaSuccess ? FKL_OK : cuda_fail(e, "reduction");
 }
 
@@ -1029,6 +1033,99 @@ fkl_status fkl_pipeline_autotune(fkl_pipeline p, int32_t n, const fkl_tensor* in
                                  fkl_tensor* out, void* stream, int32_t reps, fkl_launch_shape* best,
                                  float* best_us) {
   return fkl_pipeline_autotune_ex(p, n, ins, rois, out, stream, reps, nullptr, nullptr, best, best_us);
+}
+
+namespace {
+// Per-image slots of the per-op form, rounded up to 768 bytes (16-byte
+// vectors and 3-channel pixels in phase): an output-size float32 image, and
+// the larger slot that also holds a decoded NV12 source window.
+int64_t per_op_round(int64_t px) { return (px * 12 + 767) / 768 * 768; }
+int64_t per_op_slot_bytes(const OutDesc& od) { return per_op_round(unfused_min_px(od)); }
+int64_t per_op_slot_in_bytes(const Spec& s, const OutDesc& od, const std::vector<fkl::ResampleParams>& imgs) {
+  int64_t px = unfused_min_px(od);
+  for (const auto& r : imgs) px = std::max(px, unfused_image_px(s, od, r));
+  return per_op_round(px);
+}
+int per_op_chunk(int32_t chunk, int32_t n) {
+  const int c = chunk <= 0 ? n : std::min<int32_t>(chunk, n);
+  return std::max(1, std::min(c, kBatchCap));
+}
+fkl_status per_op_validate(fkl_pipeline p, int32_t n, const fkl_tensor* ins, const int32_t* rois,
+                           const fkl_tensor* out, OutDesc& od, std::vector<fkl::ResampleParams>& imgs) {
+  if (!p) return fail(FKL_ERR_INVALID, "null pipeline");
+  if (p->spec.family != FAM_PACKED && p->spec.family != FAM_NV12)
+    return fail(FKL_ERR_UNSUPPORTED, "the per-op form runs float image chains (READ_U8C3 / READ_NV12)");
+  return validate_batch(p, n, ins, rois, out, od, imgs);
+}
+}  // namespace
+
+fkl_status fkl_per_op_workspace_bytes(fkl_pipeline p, int32_t n, const fkl_tensor* ins, const int32_t* rois,
+                                      const fkl_tensor* out, int32_t chunk, size_t* bytes) {
+  if (!bytes) return fail(FKL_ERR_INVALID, "bytes is NULL");
+  *bytes = 0;
+  OutDesc od;
+  std::vector<fkl::ResampleParams> imgs;
+  const fkl_status st = per_op_validate(p, n, ins, rois, out, od, imgs);
+  if (st != FKL_OK) return st;
+  if (n == 0) return FKL_OK;
+  *bytes = static_cast<size_t>(per_op_chunk(chunk, n) * (per_op_slot_in_bytes(p->spec, od, imgs) +
+                                                          per_op_slot_bytes(od)));
+  return FKL_OK;
+}
+
+fkl_status fkl_execute_batch_per_op(fkl_pipeline p, int32_t n, const fkl_tensor* ins, const int32_t* rois,
+                                    fkl_tensor* out, int32_t chunk, void* workspace, size_t workspace_bytes,
+                                    void* stream, fkl_kernel_time* times, int32_t max_times, int32_t* n_times) {
+  if (n_times) *n_times = 0;
+  if (times && (!n_times || max_times < 1)) return fail(FKL_ERR_INVALID, "times needs n_times and max_times >= 1");
+  OutDesc od;
+  std::vector<fkl::ResampleParams> imgs;
+  fkl_status st = per_op_validate(p, n, ins, rois, out, od, imgs);
+  if (st != FKL_OK) return st;
+  if (n == 0) return FKL_OK;
+  const int c = per_op_chunk(chunk, n);
+  const int64_t slot_in = per_op_slot_in_bytes(p->spec, od, imgs), slot = per_op_slot_bytes(od);
+  const size_t need = static_cast<size_t>(c * (slot_in + slot));
+  if (!workspace || workspace_bytes < need || reinterpret_cast<uintptr_t>(workspace) % 256)
+    return fail(FKL_ERR_INVALID, "workspace must be >= %zu bytes and 256-byte aligned", need);
+  const cudaStream_t s = static_cast<cudaStream_t>(stream);
+  uint8_t* ws0 = static_cast<uint8_t*>(workspace);
+  uint8_t* ws1 = ws0 + c * slot_in;
+  PerOpLog log;
+  log.on = times != nullptr;
+  cudaError_t e = cudaSuccess;
+  for (int start = 0; start < n && e == cudaSuccess; start += c) {
+    fkl::OutParams o = od.p;
+    o.base += start * od.p.img;
+    e = launch_per_op_chunk(p->spec, imgs.data() + start, std::min(c, n - start), o, od.H, od.W, ws0, ws1, slot_in,
+                            slot, log, s);
+  }
+  if (e == cudaSuccess && log.failed) e = cudaErrorMemoryAllocation;
+  if (e == cudaSuccess && log.on) e = cudaStreamSynchronize(s);
+  if (e == cudaSuccess && log.on) {  // one entry per operation, in chain order
+    int k = 0;
+    for (const auto& en : log.entries) {
+      int j = 0;
+      while (j < k && std::strncmp(times[j].name, en.name, sizeof(times[j].name)) != 0) ++j;
+      if (j == k) {
+        if (k == max_times) continue;
+        std::memset(&times[k], 0, sizeof(times[k]));
+        std::snprintf(times[k].name, sizeof(times[k].name), "%s", en.name);
+        ++k;
+      }
+      float ms = 0.f;
+      if (cudaEventElapsedTime(&ms, en.start, en.stop) != cudaSuccess) ms = 0.f;
+      times[j].launches += 1;
+      times[j].bytes += en.bytes;
+      times[j].ms += ms;
+    }
+    *n_times = k;
+  }
+  for (const auto& en : log.entries) {
+    if (en.start) cudaEventDestroy(en.start);
+    if (en.stop) cudaEventDestroy(en.stop);
+  }
+  return e == cudaSuccess ? FKL_OK : cuda_fail(e, "per-op launch");
 }
 
 fkl_status fkl_execute_batch_unfused_static(fkl_pipeline p, int32_t n, const fkl_tensor* ins, const int32_t* rois,

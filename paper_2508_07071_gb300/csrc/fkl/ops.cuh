@@ -352,37 +352,42 @@ struct ResizeNV12 {
     }
   }
 
+  // The tap sums of outputs k, k+1 of the 2x span, one output per lane:
+  // per channel fl(fl(u00 + u10) + fl(u01 + u11)) of the four unit taps,
+  // before the scale to 0..255. wa, wb: word k/2 of the two luma rows'
+  // 16-byte vectors, [left(k), right(k), left(k+1), right(k+1)]; wc: the
+  // chroma word [U(k), V(k), U(k+1), V(k+1)].
+  static FKL_D void pair_sums2x(uint32_t wa, uint32_t wb, uint32_t wc, F2 (&sum)[3]) {
+    const F2* kp = reinterpret_cast<const F2*>(kNv12Pairs);
+    const F2 kY = kp[0], kC = kp[1], cy = kp[2], crv = kp[3], cgu = kp[4], cgv = kp[5], cbu = kp[6];
+    const F2 u = f2sub(f2(byte_as_float(wc, 0), byte_as_float(wc, 2)), kC);
+    const F2 v = f2sub(f2(byte_as_float(wc, 1), byte_as_float(wc, 3)), kC);
+    const F2 rv = f2mul(crv, v), guv = f2fma(cgu, u, f2mul(cgv, v)), bu = f2mul(cbu, u);
+    F2 t[4][3];  // taps row 0 left, row 0 right, row 1 left, row 1 right
+    unit_pair(f2sub(f2(byte_as_float(wa, 0), byte_as_float(wa, 2)), kY), cy, rv, guv, bu, t[0]);
+    unit_pair(f2sub(f2(byte_as_float(wa, 1), byte_as_float(wa, 3)), kY), cy, rv, guv, bu, t[1]);
+    unit_pair(f2sub(f2(byte_as_float(wb, 0), byte_as_float(wb, 2)), kY), cy, rv, guv, bu, t[2]);
+    unit_pair(f2sub(f2(byte_as_float(wb, 1), byte_as_float(wb, 3)), kY), cy, rv, guv, bu, t[3]);
+#pragma unroll
+    for (int ch = 0; ch < 3; ++ch) sum[ch] = f2add(f2add(t[0][ch], t[2][ch]), f2add(t[1][ch], t[3][ch]));
+  }
+
   // The arithmetic of the 2x span from the 16-byte words of the two luma
   // rows (a, b) and the chroma row (c), wherever they were loaded from.
   template <int V>
   static FKL_D void compute2x(const uint4 (&a)[V / 8], const uint4 (&b)[V / 8], const uint4 (&c)[V / 8],
                               F3 (&out)[V]) {
-    const F2* kp = reinterpret_cast<const F2*>(kNv12Pairs);
-    const F2 kY = kp[0], kC = kp[1], cy = kp[2], crv = kp[3], cgu = kp[4], cgv = kp[5], cbu = kp[6],
-             c6375 = kp[7];
+    const F2 c6375 = reinterpret_cast<const F2*>(kNv12Pairs)[7];
 #pragma unroll
     for (int k = 0; k < V; k += 2) {
       // outputs k, k+1 use bytes 2k .. 2k+3 of each row: word (k % 8) / 2 of
-      // vector k / 8 holds [left(k), right(k), left(k+1), right(k+1)] for
-      // luma and [U(k), V(k), U(k+1), V(k+1)] for chroma.
+      // vector k / 8
       const int vi = k / 8, wi = (k % 8) / 2;
-      const uint32_t wa = reinterpret_cast<const uint32_t*>(&a[vi])[wi];
-      const uint32_t wb = reinterpret_cast<const uint32_t*>(&b[vi])[wi];
-      const uint32_t wc = reinterpret_cast<const uint32_t*>(&c[vi])[wi];
-      const F2 u = f2sub(f2(byte_as_float(wc, 0), byte_as_float(wc, 2)), kC);
-      const F2 v = f2sub(f2(byte_as_float(wc, 1), byte_as_float(wc, 3)), kC);
-      const F2 rv = f2mul(crv, v), guv = f2fma(cgu, u, f2mul(cgv, v)), bu = f2mul(cbu, u);
-      F2 t[4][3];  // taps row 0 left, row 0 right, row 1 left, row 1 right
-      unit_pair(f2sub(f2(byte_as_float(wa, 0), byte_as_float(wa, 2)), kY), cy, rv, guv, bu, t[0]);
-      unit_pair(f2sub(f2(byte_as_float(wa, 1), byte_as_float(wa, 3)), kY), cy, rv, guv, bu, t[1]);
-      unit_pair(f2sub(f2(byte_as_float(wb, 0), byte_as_float(wb, 2)), kY), cy, rv, guv, bu, t[2]);
-      unit_pair(f2sub(f2(byte_as_float(wb, 1), byte_as_float(wb, 3)), kY), cy, rv, guv, bu, t[3]);
+      F2 sum[3];
+      pair_sums2x(reinterpret_cast<const uint32_t*>(&a[vi])[wi], reinterpret_cast<const uint32_t*>(&b[vi])[wi],
+                  reinterpret_cast<const uint32_t*>(&c[vi])[wi], sum);
 #pragma unroll
-      for (int ch = 0; ch < 3; ++ch) {
-        const F2 left = f2add(t[0][ch], t[2][ch]);
-        const F2 right = f2add(t[1][ch], t[3][ch]);
-        f2split(f2mul(f2add(left, right), c6375), out[k].v[ch], out[k + 1].v[ch]);
-      }
+      for (int ch = 0; ch < 3; ++ch) f2split(f2mul(sum[ch], c6375), out[k].v[ch], out[k + 1].v[ch]);
     }
   }
 
@@ -457,6 +462,39 @@ struct DecodeNV12 {
   using ParamsType = ResampleParams;
   using OutputType = F3;
   static FKL_D F3 exec(const Point& pt, const ParamsType& p) { return nv12_unit(p, p.rx + pt.x, p.ry + pt.y); }
+
+  // V consecutive pixels of one row, from 4-byte words of the luma and the
+  // chroma row when the first pixel's column is a multiple of 4 and the
+  // pitch too (the same arithmetic as exec, one chroma term per pixel pair).
+  template <int V>
+  static FKL_D void exec_span(const Point& pt, const ParamsType& p, F3 (&out)[V]) {
+    const int sx = p.rx + pt.x, sy = p.ry + pt.y;
+    if constexpr (V % 4 == 0) {
+      if ((sx & 3) == 0 && (p.pitch & 3) == 0 && (reinterpret_cast<uintptr_t>(p.src) & 3) == 0 &&
+          (reinterpret_cast<uintptr_t>(p.uv) & 3) == 0) {
+        const uint32_t* yw = reinterpret_cast<const uint32_t*>(p.src + static_cast<int64_t>(sy) * p.pitch + sx);
+        const uint32_t* cw = reinterpret_cast<const uint32_t*>(p.uv + static_cast<int64_t>(sy >> 1) * p.pitch + sx);
+#pragma unroll
+        for (int i = 0; i < V / 4; ++i) {
+          const uint32_t wy = __ldg(yw + i), wc = __ldg(cw + i);
+#pragma unroll
+          for (int h = 0; h < 2; ++h) {  // chroma sample h serves pixels 2h, 2h + 1
+            const float uf = static_cast<float>((wc >> (16 * h)) & 0xFFu) - 128.f;
+            const float vf = static_cast<float>((wc >> (16 * h + 8)) & 0xFFu) - 128.f;
+            const ChromaTerms t = chroma_terms(uf, vf);
+#pragma unroll
+            for (int j = 0; j < 2; ++j) {
+              const float yf = static_cast<float>((wy >> (8 * (2 * h + j))) & 0xFFu) - 16.f;
+              out[4 * i + 2 * h + j] = yuv_to_unit(yf, t);
+            }
+          }
+        }
+        return;
+      }
+    }
+#pragma unroll
+    for (int k = 0; k < V; ++k) out[k] = exec(Point{pt.x + k, pt.y, pt.z}, p);
+  }
 };
 
 // Packed float32 3-channel image (an intermediate of the unfused chains),
@@ -484,6 +522,45 @@ struct ResizeF32C3T {
     if constexpr (kUnit) return scale255(b);
     return b;
   }
+
+  // V outputs of one row of an exact 2x downscale, inside the window: the
+  // taps of output k are source pixels 2k, 2k + 1 of two rows, read as
+  // 16-byte vectors (the 24 V bytes of each row start 16-byte aligned); the
+  // blend is blend_float's with its weights, which are exactly 1/2 here, so
+  // the bits are exec's. Other spans take exec pixel by pixel.
+  template <int V>
+  static FKL_D void exec_span(const Point& pt, const ParamsType& p, F3 (&out)[V]) {
+    const int lx = pt.x - p.ox, ly = pt.y - p.oy;
+    if constexpr (V % 2 == 0) {
+      const int sx = p.rx + 2 * lx;
+      if ((p.flags & kExact2x) && ly >= 0 && ly < p.dh && lx >= 0 && lx + V <= p.dw && (sx & 3) == 0 &&
+          (p.pitch & 15) == 0 && (reinterpret_cast<uintptr_t>(p.src) & 15) == 0) {
+        const int64_t y0 = p.ry + 2 * ly;
+        const float4* r0 = reinterpret_cast<const float4*>(p.src + y0 * p.pitch) + 3 * sx / 4;
+        const float4* r1 = reinterpret_cast<const float4*>(p.src + (y0 + 1) * p.pitch) + 3 * sx / 4;
+        float a[6 * V], b[6 * V];  // 2 V source pixels x 3 channels of each row
+#pragma unroll
+        for (int i = 0; i < 3 * V / 2; ++i) {
+          const float4 u = __ldg(r0 + i), w = __ldg(r1 + i);
+          a[4 * i] = u.x, a[4 * i + 1] = u.y, a[4 * i + 2] = u.z, a[4 * i + 3] = u.w;
+          b[4 * i] = w.x, b[4 * i + 1] = w.y, b[4 * i + 2] = w.z, b[4 * i + 3] = w.w;
+        }
+#pragma unroll
+        for (int k = 0; k < V; ++k) {
+#pragma unroll
+          for (int c = 0; c < 3; ++c) {
+            const float left = __fadd_rn(__fmul_rn(0.5f, a[6 * k + c]), __fmul_rn(0.5f, b[6 * k + c]));
+            const float right = __fadd_rn(__fmul_rn(0.5f, a[6 * k + 3 + c]), __fmul_rn(0.5f, b[6 * k + 3 + c]));
+            const float o = __fadd_rn(__fmul_rn(0.5f, left), __fmul_rn(0.5f, right));
+            out[k].v[c] = kUnit ? __fmul_rn(o, 255.f) : o;
+          }
+        }
+        return;
+      }
+    }
+#pragma unroll
+    for (int k = 0; k < V; ++k) out[k] = exec(Point{pt.x + k, pt.y, pt.z}, p);
+  }
 };
 using ResizeF32C3 = ResizeF32C3T<false>;
 
@@ -494,6 +571,28 @@ struct ReadF32C3 {
   using OutputType = F3;
   static FKL_D F3 exec(const Point& pt, const ParamsType& p) {
     return ResizeF32C3::load(p, p.rx + pt.x, p.ry + pt.y);
+  }
+  // V pixels (12 V bytes) as 16-byte vectors when they start 16-byte aligned.
+  template <int V>
+  static FKL_D void exec_span(const Point& pt, const ParamsType& p, F3 (&out)[V]) {
+    const int sx = p.rx + pt.x;
+    if constexpr (V % 4 == 0) {
+      if ((sx & 3) == 0 && (p.pitch & 15) == 0 && (reinterpret_cast<uintptr_t>(p.src) & 15) == 0) {
+        const float4* q =
+            reinterpret_cast<const float4*>(p.src + static_cast<int64_t>(p.ry + pt.y) * p.pitch) + 3 * sx / 4;
+        float f[3 * V];
+#pragma unroll
+        for (int i = 0; i < 3 * V / 4; ++i) {
+          const float4 u = __ldcs(q + i);
+          f[4 * i] = u.x, f[4 * i + 1] = u.y, f[4 * i + 2] = u.z, f[4 * i + 3] = u.w;
+        }
+#pragma unroll
+        for (int k = 0; k < V; ++k) out[k] = F3{{f[3 * k], f[3 * k + 1], f[3 * k + 2]}};
+        return;
+      }
+    }
+#pragma unroll
+    for (int k = 0; k < V; ++k) out[k] = exec(Point{pt.x + k, pt.y, pt.z}, p);
   }
 };
 

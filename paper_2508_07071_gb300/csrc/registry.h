@@ -76,11 +76,18 @@ cudaError_t launch_nv12_bf16(const LaunchCtx& c);
 cudaError_t launch_nv12_e4m3(const LaunchCtx& c);
 // Integer chains (k_int.cu).
 cudaError_t launch_int(const LaunchCtx& c);
-// ReduceDPP over the ROp and COps of a float image chain (k_reduce.cu):
-// accumulates into `acc` (initialised by the caller); `finalize_reduce`
-// turns the accumulator into the float statistics of include/fkl.h.
-cudaError_t launch_reduce(const LaunchCtx& c, fkl::ReduceAcc* acc);
-cudaError_t finalize_reduce(const fkl::ReduceAcc* acc, double count, float* stats, cudaStream_t st);
+// ReduceDPP over a float image chain (k_reduce.cu): launch_reduce reduces
+// the ROp's values over each image's placed window into `acc` (initialised
+// by the caller) and adds its work split to `info`; finalize_reduce maps the
+// accumulator through the chain's COps into the statistics of include/fkl.h
+// (`count` output pixels per channel, `fill_count` of them fill pixels).
+struct ReduceLaunch {
+  int64_t jobs = 0;  // jobs of all reduction launches
+  int grid = 0;      // blocks of the largest launch
+};
+cudaError_t launch_reduce(const LaunchCtx& c, fkl::ReduceAcc* acc, ReduceLaunch& info);
+cudaError_t finalize_reduce(const Spec& s, const fkl::ReduceAcc* acc, double count, double fill_count,
+                            const ReduceLaunch& info, float* stats, cudaStream_t st);
 // Vertical chain (k_vchain.cu): one fused launch per chunk of ops.
 constexpr int kVChainCap = 4096;
 cudaError_t launch_vchain(const Spec& s, const fkl_launch_shape& shape, const void* in, float* out,
@@ -102,6 +109,31 @@ cudaError_t launch_unfused_image(const Spec& s, const fkl::ResampleParams& img,
                                  void* ws0, void* ws1, cudaStream_t stream);
 cudaError_t launch_unfused_vchain(const Spec& s, const void* in, float* out, int64_t n,
                                   cudaStream_t stream);
+
+// Optional per-kernel timing of the per-op form: events around each launch
+// (only when `on`), with the kernel's name and algorithmic bytes.
+struct PerOpLog {
+  struct Entry {
+    const char* name;
+    double bytes;
+    cudaEvent_t start = nullptr, stop = nullptr;
+  };
+  bool on = false;
+  bool failed = false;
+  std::vector<Entry> entries;
+  void begin(const char* name, double bytes, cudaStream_t st);
+  void end(cudaStream_t st);
+};
+
+// The per-op form over a chunk of n <= kBatchCap images (k_unfused.cu): one
+// kernel per operation over all n images. ws0 holds n slots of `slot_in`
+// bytes (the NV12 decode at source size, later reused at output size), ws1 n
+// slots of `slot` bytes (one output-size image each); slot_in >= slot, both
+// multiples of 768, so the output-size images of a chunk are contiguous in
+// either buffer.
+cudaError_t launch_per_op_chunk(const Spec& s, const fkl::ResampleParams* imgs, int n, const fkl::OutParams& out,
+                                int H, int W, uint8_t* ws0, uint8_t* ws1, int64_t slot_in, int64_t slot,
+                                PerOpLog& log, cudaStream_t stream);
 
 // Launch shapes compiled for a family/dtype (the autotuner's search space).
 std::vector<fkl_launch_shape> shapes_for(const Spec& s);

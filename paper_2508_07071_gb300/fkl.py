@@ -111,6 +111,13 @@ EXPORTS = {
                                                         ctypes.POINTER(fkl_tensor),
                                                         ctypes.POINTER(ctypes.c_int32),
                                                         ctypes.POINTER(fkl_tensor), ctypes.c_void_p]),
+    "fkl_per_op_workspace_bytes": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int32, ctypes.POINTER(fkl_tensor),
+                                                  ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(fkl_tensor),
+                                                  ctypes.c_int32, ctypes.POINTER(ctypes.c_size_t)]),
+    "fkl_execute_batch_per_op": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int32, ctypes.POINTER(fkl_tensor),
+                                                ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(fkl_tensor),
+                                                ctypes.c_int32, ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p,
+                                                ctypes.c_void_p, ctypes.c_int32, ctypes.POINTER(ctypes.c_int32)]),
     "fkl_pipeline_kernel_name": (ctypes.c_char_p, [ctypes.c_void_p]),
     "fkl_pipeline_get_shape": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(fkl_launch_shape)]),
     "fkl_pipeline_set_shape": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(fkl_launch_shape)]),
@@ -486,6 +493,38 @@ def fkl_execute_batch_unfused(p: int, ins: Sequence[fkl_tensor], rois, out: fkl_
     _check(_lib.fkl_execute_batch_unfused(p, len(ins), arr, keep[1] if keep else None,
                                           ctypes.byref(out), workspace_ptr, workspace_bytes,
                                           _stream(stream)))
+
+
+class fkl_kernel_time(ctypes.Structure):
+    _fields_ = [("name", ctypes.c_char * 32), ("launches", ctypes.c_int32), ("bytes", ctypes.c_double),
+                ("ms", ctypes.c_double)]
+
+
+def fkl_per_op_workspace_bytes(p: int, ins: Sequence[fkl_tensor], rois, out: fkl_tensor, chunk: int = 0) -> int:
+    arr = (fkl_tensor * max(1, len(ins)))(*ins)
+    keep = _rois(rois)
+    n = ctypes.c_size_t()
+    _check(_lib.fkl_per_op_workspace_bytes(p, len(ins), arr, keep[1] if keep else None, ctypes.byref(out),
+                                           int(chunk), ctypes.byref(n)))
+    return n.value
+
+
+def fkl_execute_batch_per_op(p: int, ins: Sequence[fkl_tensor], rois, out: fkl_tensor, workspace_ptr: int,
+                             workspace_bytes: int, chunk: int = 0, stream=None, timed: bool = False):
+    """The unfused chain with one kernel per op over the batch; with
+    `timed`, returns [(name, launches, bytes, ms)] per operation (the call
+    then synchronizes the stream)."""
+    arr = (fkl_tensor * max(1, len(ins)))(*ins)
+    keep = _rois(rois)
+    times = (fkl_kernel_time * 16)() if timed else None
+    nt = ctypes.c_int32()
+    _check(_lib.fkl_execute_batch_per_op(p, len(ins), arr, keep[1] if keep else None, ctypes.byref(out),
+                                         int(chunk), workspace_ptr, workspace_bytes, _stream(stream),
+                                         ctypes.cast(times, ctypes.c_void_p) if timed else None, 16,
+                                         ctypes.byref(nt)))
+    if not timed:
+        return None
+    return [(t.name.decode(), t.launches, t.bytes, t.ms) for t in times[:nt.value]]
 
 
 def fkl_execute_batch_unfused_static(p: int, ins: Sequence[fkl_tensor], rois, out: fkl_tensor,

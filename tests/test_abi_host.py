@@ -340,3 +340,35 @@ def test_error_messages_are_kept_per_thread_and_truncated(F):
         assert F._lib.fkl_last_error().decode() == here
     finally:
         F.fkl_pipeline_destroy(p)
+
+
+def test_per_op_workspace_and_validation(F):
+    """The per-op form sizes two ping-pong sets of chunk intermediates and
+    checks its workspace on the host, before any launch."""
+    from paper_2508_07071_gb300 import workloads as W
+    p = F.fkl_pipeline_create(W.nv12_letterbox_chain(F.FKL_BF16, out=64))
+    try:
+        src = F._tensor(0x1000, (128, 256), 256, F.FKL_U8, F.FKL_LAYOUT_NV12)
+        out = F._tensor(0x2000, (5, 3, 64, 64), 128, F.FKL_BF16, F.FKL_LAYOUT_NCHW)
+        slot_in = (256 * 128 * 12 + 767) // 768 * 768   # the decoded source window
+        slot = (64 * 64 * 12 + 767) // 768 * 768        # one output-size image
+        each = slot_in + slot
+        assert F.fkl_per_op_workspace_bytes(p, [src] * 5, None, out, 0) == 5 * each
+        assert F.fkl_per_op_workspace_bytes(p, [src] * 5, None, out, 2) == 2 * each
+        assert F.fkl_per_op_workspace_bytes(p, [src] * 5, None, out, 999) == 5 * each
+        with pytest.raises(F.FklError) as ei:          # workspace too small: refused before any launch
+            F.fkl_execute_batch_per_op(p, [src] * 5, None, out, 0x100000, 5 * each - 256, stream=0)
+        assert ei.value.status == F.FKL_ERR_INVALID
+        with pytest.raises(F.FklError) as ei:          # unaligned workspace
+            F.fkl_execute_batch_per_op(p, [src] * 5, None, out, 0x100010, 5 * each, stream=0)
+        assert ei.value.status == F.FKL_ERR_INVALID
+    finally:
+        F.fkl_pipeline_destroy(p)
+    pv = F.fkl_pipeline_create(W.vertical_chain([0], [2.0]))
+    try:
+        lin = F._tensor(0x3000, (10,), 0, F.FKL_F32, F.FKL_LAYOUT_LINEAR)
+        with pytest.raises(F.FklError) as ei:
+            F.fkl_per_op_workspace_bytes(pv, [lin], None, lin, 0)
+        assert ei.value.status == F.FKL_ERR_UNSUPPORTED
+    finally:
+        F.fkl_pipeline_destroy(pv)

@@ -532,6 +532,75 @@ def test_reduce_stats_normalised_packed(F, W):
     assert float(out.abs().sum()) == 0.0               # the reduction writes no output
 
 
+def _reduce_split(stats):
+    """(float statistics, jobs, blocks) of a stats buffer."""
+    st = stats.cpu()
+    return st[:12].numpy().astype(np.float64), int(st.view(torch.int32)[12]), int(st.view(torch.int32)[13])
+
+
+def test_reduce_many_jobs_per_block_against_the_oracle_and_the_write(F, W):
+    """The reduction's persistent grid with several jobs per block (the job
+    count is checked against the grid): statistics against the oracle's, the
+    extremes equal bit for bit to those of the fused chain's float32 output,
+    and the dynamic FP8 codes of sampled frames within 1 ulp."""
+    n = 40
+    frames = synth.nv12_frames(19, n, 720, 1280)
+    dev = torch.from_numpy(frames).cuda()
+    ins = [F.as_fkl(dev[i], F.FKL_LAYOUT_NV12) for i in range(n)]
+    p = F.Pipeline(W.nv12_letterbox_chain(F.FKL_E4M3, scale=1.0))
+    out = torch.zeros((n, 3, 640, 640), dtype=torch.float8_e4m3fn, device="cuda")
+    o = F.as_fkl(out, F.FKL_LAYOUT_NCHW)
+    stats = torch.zeros(32, device="cuda")
+    F.fkl_reduce_batch(p.handle, ins, None, o, stats.data_ptr())
+    F.fkl_execute_batch_scaled(p.handle, ins, None, o, stats.data_ptr() + 11 * 4)
+    f32 = run_batch(F, W.nv12_letterbox_chain(F.FKL_F32), [dev[i] for i in range(n)], None, (n, 3, 640, 640),
+                    "f32", layout_in=F.FKL_LAYOUT_NV12)
+    torch.cuda.synchronize()
+    st, jobs, grid = _reduce_split(stats)
+    assert jobs > 2 * grid > 0, (jobs, grid)
+    per_c = f32.permute(1, 0, 2, 3).reshape(3, -1)
+    assert np.array_equal(st[0:3].astype(np.float32), per_c.min(dim=1).values.cpu().numpy())
+    assert np.array_equal(st[3:6].astype(np.float32), per_c.max(dim=1).values.cpu().numpy())
+    vals = np.stack([O.preprocess_nv12(f, 640, 640, pad=114.0, mul=1 / 255) for f in frames])
+    want = O.reduce_stats(vals)
+    check_f32(st[0:3], want["min"], "min")
+    check_f32(st[3:6], want["max"], "max")
+    np.testing.assert_allclose(st[6:9], want["mean"], rtol=1e-6)
+    check_f32(st[9], want["amax"], "amax")
+    check_f32(st[10], want["scale"], "scale")
+    for i in (0, n // 2, n - 1):
+        check_lowp(to_numpy(out[i]), vals[i] / np.float32(st[10]), "e4m3", 1.0, f"dynamic fp8 frame {i}")
+    assert out.view(torch.uint8).max().item() == 0x7E
+
+
+@pytest.mark.parametrize("swap", [True, False])
+def test_reduce_decreasing_chain(F, W, swap):
+    """Negative Mul and Div make the chain decreasing on every channel: the
+    minimum comes from the largest read value. Extremes equal the float32
+    write's; mean and amax match the oracle."""
+    src = synth.packed_image(29, 300, 500)
+    rois = np.array([[0, 0, 500, 300], [17, 9, 333, 201], [100, 50, 64, 32]], np.int32)
+    mul, sub, div = (-1 / 255, 2 / 255, -0.5), (0.25, -0.5, 1.0), (-0.229, 0.5, -2.0)
+    ops = [F.read_u8c3(), F.resize(97, 61)] + ([F.swap_rb()] if swap else []) + \
+        [F.mul(mul), F.sub(sub), F.div(div), F.write_split(F.FKL_F32)]
+    d = torch.from_numpy(src).cuda()
+    got = run_batch(F, ops, [d] * 3, rois, (3, 3, 61, 97), "f32")
+    p = F.Pipeline(ops)
+    stats = torch.zeros(32, device="cuda")
+    F.fkl_reduce_batch(p.handle, [F.as_fkl(d)] * 3, rois, F.as_fkl(got, F.FKL_LAYOUT_NCHW), stats.data_ptr())
+    torch.cuda.synchronize()
+    st, _, _ = _reduce_split(stats)
+    per_c = got.permute(1, 0, 2, 3).reshape(3, -1)
+    assert np.array_equal(st[0:3].astype(np.float32), per_c.min(dim=1).values.cpu().numpy())
+    assert np.array_equal(st[3:6].astype(np.float32), per_c.max(dim=1).values.cpu().numpy())
+    vals = O.preprocess_packed_batch([src] * 3, rois, 97, 61, swap=swap, mul=mul, sub=sub, div=div)
+    want = O.reduce_stats(vals)
+    check_f32(st[0:3], want["min"], "min")
+    check_f32(st[3:6], want["max"], "max")
+    np.testing.assert_allclose(st[6:9], want["mean"], rtol=1e-5, atol=1e-6)
+    check_f32(st[9], want["amax"], "amax")
+
+
 @pytest.mark.parametrize("fmt", ["e4m3", "f16"])
 def test_nv12_full_batch_autotuned_sampled(F, W, fmt):
     """The bench's configuration: 256 frames, autotuned launch shape."""
@@ -1001,3 +1070,84 @@ def test_reduce_pillarbox_fill_columns(F, W, src):
     check_f32(st[3:6], want["max"], "max")
     np.testing.assert_allclose(st[6:9], want["mean"], rtol=1e-6)
     check_f32(st[9], want["amax"], "amax")
+
+
+# ------------------------------------------------------------------ the per-op form over the batch
+
+
+def _per_op(F, ops, srcs, rois, out_shape, fmt, layout_in=None, chunk=0, timed=False):
+    p = F.Pipeline(ops)
+    out = torch.full(out_shape, float("nan") if fmt not in ("u8", "e4m3") else 0, dtype=tdtype(fmt), device="cuda")
+    layout = F.FKL_LAYOUT_NCHW if out_shape[1] == 3 else F.FKL_LAYOUT_NHWC
+    ins = [F.as_fkl(s, layout_in) for s in srcs]
+    o = F.as_fkl(out, layout)
+    nb = F.fkl_per_op_workspace_bytes(p.handle, ins, rois, o, chunk)
+    ws = torch.empty(max(nb, 256), dtype=torch.uint8, device="cuda")
+    rep = F.fkl_execute_batch_per_op(p.handle, ins, rois, o, ws.data_ptr(), nb, chunk=chunk, timed=timed)
+    torch.cuda.synchronize()
+    return out, rep, nb
+
+
+@pytest.mark.parametrize("fmt", ["bf16", "e4m3", "f32", "f16"])
+def test_per_op_nv12_equals_fused_bitwise(F, W, fmt):
+    """One kernel per op over the batch (decode, letterbox, x1/255, split +
+    cast) gives the fused kernel's bytes; chunks of 3 frames (ragged last
+    chunk) give the same."""
+    frames = synth.nv12_frames(31, 5, 720, 1280)
+    dev = [torch.from_numpy(f).cuda() for f in frames]
+    ops = W.nv12_letterbox_chain(code(F, fmt))
+    fused = run_batch(F, ops, dev, None, (5, 3, 640, 640), fmt, layout_in=F.FKL_LAYOUT_NV12)
+    bits = torch.int8 if fmt == "e4m3" else (torch.int32 if fmt == "f32" else torch.int16)
+    for chunk in (0, 3):
+        got, _, _ = _per_op(F, ops, dev, None, (5, 3, 640, 640), fmt, F.FKL_LAYOUT_NV12, chunk=chunk)
+        assert torch.equal(got.view(bits), fused.view(bits)), chunk
+    want = O.preprocess_nv12(frames[4], 640, 640, pad=114.0, mul=1 / 255)
+    check_output(got[4], want, fmt, W.E4M3_SCALE if fmt == "e4m3" else 1.0, "per-op frame 4")
+
+
+def test_per_op_packed_crops_equal_fused_and_report_kernels(F, W):
+    """The 50-crop normalise chain: one kernel per op over all crops equals
+    the fused kernel bit for bit; the timed call names every kernel in chain
+    order with its launches, algorithmic bytes and time."""
+    cfg = W.HF
+    src = synth.packed_image(1, cfg["src_h"], cfg["src_w"])
+    rois = synth.crop_rois(1, cfg["n"], cfg["src_w"], cfg["src_h"], cfg["w_range"], cfg["h_range"])
+    d = torch.from_numpy(src).cuda()
+    ops = W.normalize_chain(cfg["out_w"], cfg["out_h"])
+    shape = (cfg["n"], 3, cfg["out_h"], cfg["out_w"])
+    fused = run_batch(F, ops, [d] * cfg["n"], rois, shape, "f32")
+    got, rep, nb = _per_op(F, ops, [d] * cfg["n"], rois, shape, "f32", timed=True)
+    assert torch.equal(got.view(torch.int32), fused.view(torch.int32))
+    names = [r[0] for r in rep]
+    assert names == ["crop + resize u8 -> f32", "BGR <-> RGB", "multiply", "subtract", "divide", "split + cast"]
+    px = cfg["n"] * cfg["out_h"] * cfg["out_w"]
+    assert all(r[1] == 1 and r[3] > 0 for r in rep), rep
+    assert rep[1][2] == 24 * px and rep[5][2] == 24 * px  # read 12 B + write 12 B per pixel
+    assert nb == 2 * cfg["n"] * ((cfg["out_h"] * cfg["out_w"] * 12 + 767) // 768 * 768)  # packed: both slots output-size
+    # chunks of 16: four rounds of every kernel, the same bytes
+    got, rep, _ = _per_op(F, ops, [d] * cfg["n"], rois, shape, "f32", chunk=16, timed=True)
+    assert torch.equal(got.view(torch.int32), fused.view(torch.int32))
+    assert all(r[1] == 4 for r in rep), rep
+
+
+def test_per_op_nv12_mixed_windows_and_normalise(F, W):
+    """Frames of two sizes (one decode launch per run of equal windows), a
+    general (non-2x) letterbox and the full normalise chain."""
+    small = synth.nv12_frames(32, 2, 360, 640)
+    big = synth.nv12_frames(33, 2, 720, 1280)
+    srcs = [torch.from_numpy(f).cuda() for f in (small[0], big[0], big[1], small[1])]
+    ops = [F.read_nv12(), F.letterbox(300, 200, 114.0), F.swap_rb(), F.mul(W.INV255), F.sub(W.IMAGENET_MEAN),
+           F.div(W.IMAGENET_STD), F.write_split(F.FKL_F16)]
+    fused = run_batch(F, ops, srcs, None, (4, 3, 200, 300), "f16", layout_in=F.FKL_LAYOUT_NV12)
+    got, rep, _ = _per_op(F, ops, srcs, None, (4, 3, 200, 300), "f16", F.FKL_LAYOUT_NV12, timed=True)
+    assert torch.equal(got.view(torch.int16), fused.view(torch.int16))
+    assert rep[0][0] == "decode NV12 -> RGB f32" and rep[0][1] == 3  # runs: small, big x2, small
+
+
+def test_per_op_refuses_other_families(F, W):
+    p = F.Pipeline(W.integer_chain())
+    src = torch.zeros((8, 8, 3), dtype=torch.uint8, device="cuda")
+    out = torch.zeros((1, 8, 8, 3), dtype=torch.uint8, device="cuda")
+    with pytest.raises(F.FklError) as ei:
+        F.fkl_per_op_workspace_bytes(p.handle, [F.as_fkl(src)], None, F.as_fkl(out, F.FKL_LAYOUT_NHWC))
+    assert ei.value.status == F.FKL_ERR_UNSUPPORTED

@@ -159,3 +159,52 @@ def test_request_times_and_destroy_with_work_in_flight(F, pool):
     t0 = time.time()
     F.fkl_server_destroy(srv)
     assert time.time() - t0 < 15.0
+
+
+def test_largest_and_smallest_images_match_oracle(F):
+    """The config's extremes (3840x2160, 320x240 and the two mixed shapes),
+    in one request and in a mix with others, element by element against the
+    oracle: the resize factors and the 64-bit row offsets of a 4K frame."""
+    from paper_2508_07071_gb300 import workloads as W
+    sizes = [(2160, 3840), (240, 320), (240, 3840), (2160, 320), (721, 1283)]
+    imgs = [torch.from_numpy(synth.packed_image(500 + k, h, w)).pin_memory() for k, (h, w) in enumerate(sizes)]
+    p = pipeline(F)
+    for mode in (F.FKL_SERVE_PERSISTENT, F.FKL_SERVE_UNFUSED):
+        srv = F.fkl_server_create(p.handle, mode, max_inflight=8, arena_bytes=1 << 30)
+        try:
+            reqs = [[0, 1, 2, 3, 4], [4, 3], [0], [1, 0]]
+            outs = serve(F, srv, imgs, reqs)
+        finally:
+            F.fkl_server_destroy(srv)
+        want = []
+        for im in imgs:
+            src = im.numpy()
+            want.append(O.preprocess_packed(src, (0, 0, src.shape[1], src.shape[0]), OUT, OUT, swap=True,
+                                            mul=1 / 255, sub=W.IMAGENET_MEAN, div=W.IMAGENET_STD))
+        for r, out in zip(reqs, outs):
+            for j, idx in enumerate(r):
+                check_output(out[j], want[idx], "f16", 1.0, f"mode {mode} image {sizes[idx]}")
+
+
+def test_requests_overlap_on_the_device(F, pool):
+    """Continuous batching: requests submitted together are admitted and
+    published while earlier ones are still running, so some later request's
+    work is on the device (published to the kernel's queue) before an earlier
+    request has finished."""
+    p = pipeline(F)
+    srv = F.fkl_server_create(p.handle, F.FKL_SERVE_PERSISTENT, max_inflight=16, arena_bytes=1 << 30)
+    try:
+        reqs = make_requests(pool, 12, 7, max_images=6)
+        ids = [F.fkl_server_submit(srv, [F.as_fkl(pool[i]) for i in r]) for r in reqs]
+        infos = []
+        for rid in ids:
+            F.fkl_server_wait(srv, rid, 30000)
+            infos.append(F.fkl_server_request_info(srv, rid))
+            F.fkl_server_release(srv, rid)
+    finally:
+        F.fkl_server_destroy(srv)
+    overlapped = [(i, j) for i in range(len(infos)) for j in range(i + 1, len(infos))
+                  if infos[j].t_ready < infos[i].t_done and infos[j].t_admit < infos[i].t_done]
+    assert overlapped, [(x.t_admit, x.t_ready, x.t_done) for x in infos]
+    # FIFO admission: no request is admitted before one submitted earlier
+    assert all(infos[k].t_admit <= infos[k + 1].t_admit for k in range(len(infos) - 1))
