@@ -389,6 +389,8 @@ const int kBlocks[][2] = {{8, 16}, {16, 8}, {16, 16}, {32, 4}, {32, 8}, {64, 2},
 // 24-point sweep (threads 128/256, rows 2/4/8, stages 2/3/4/6) on 256 frames
 // 1280x720 -> 640x640; deeper rings and longer jobs only lowered occupancy.
 const int kStaged[][3] = {{128, 4, 2}, {128, 2, 2}, {128, 4, 3}, {256, 8, 2}};
+// Tile-staged packed shapes {threads x, threads y}: tiles of (x * vec) x y outputs.
+const int kTiles[][2] = {{16, 8}, {32, 8}, {16, 16}, {32, 4}, {8, 16}};
 }
 // ---------------------------------------------------------------------------
 // Scratch for fkl_execute_batch_unfused_static: a fixed device array that
@@ -484,6 +486,11 @@ std::vector<fkl_launch_shape> shapes_for(const Spec& s) {
     for (int ry : {1, 2}) {
       if (v > 8 && ry > 1) continue;  // not compiled (register budget)
       for (const auto& b : kBlocks) out.push_back(fkl_launch_shape{v, b[0], b[1], ry});
+    }
+  if (s.family == FAM_PACKED)  // tile-staged packed reader: {vec, tile threads x, y, -1}
+    for (int v : vecs) {
+      if (v > 4) continue;
+      for (const auto& b : kTiles) out.push_back(fkl_launch_shape{v, b[0], b[1], -1});
     }
   if (s.family == FAM_NV12 && s.split)  // row-staged kernel: {vec, threads, rows per job, -stages}
     for (int v : vecs) {

@@ -144,12 +144,10 @@ struct ResizeU8C3T {
   using OutputType = F3;
   static constexpr bool kPlaced = true;  // the pad value outside the placed window
 
-  static FKL_D F3 blend(const uint8_t* row0, const uint8_t* row1, const AxisTap& tx,
-                        int Dx, const AxisTap& ty, int Dy, float inv_area) {
-    const uint8_t* p00 = row0 + 3 * tx.i0;
-    const uint8_t* p01 = row0 + 3 * tx.i1;
-    const uint8_t* p10 = row1 + 3 * tx.i0;
-    const uint8_t* p11 = row1 + 3 * tx.i1;
+  // The blend of four taps' bytes: s[0] = S(x0, y0), s[1] = S(x1, y0),
+  // s[2] = S(x0, y1), s[3] = S(x1, y1), each channel exact in integers.
+  static FKL_D F3 blend_bytes(const uint32_t (&s)[4][3], const AxisTap& tx, int Dx, const AxisTap& ty, int Dy,
+                              float inv_area) {
     const uint32_t wx1 = static_cast<uint32_t>(tx.w1);
     const uint32_t wx0 = static_cast<uint32_t>(Dx - tx.w1);
     const uint32_t wy1 = static_cast<uint32_t>(ty.w1);
@@ -157,12 +155,29 @@ struct ResizeU8C3T {
     F3 o;
 #pragma unroll
     for (int c = 0; c < 3; ++c) {
-      const uint32_t top = wx0 * load_u8<kCoherent>(p00 + c) + wx1 * load_u8<kCoherent>(p01 + c);
-      const uint32_t bot = wx0 * load_u8<kCoherent>(p10 + c) + wx1 * load_u8<kCoherent>(p11 + c);
+      const uint32_t top = wx0 * s[0][c] + wx1 * s[1][c];
+      const uint32_t bot = wx0 * s[2][c] + wx1 * s[3][c];
       const uint64_t n = static_cast<uint64_t>(wy0) * top + static_cast<uint64_t>(wy1) * bot;
       o.v[c] = __fmul_rn(__ull2float_rn(n), inv_area);
     }
     return o;
+  }
+
+  static FKL_D F3 blend(const uint8_t* row0, const uint8_t* row1, const AxisTap& tx,
+                        int Dx, const AxisTap& ty, int Dy, float inv_area) {
+    const uint8_t* p00 = row0 + 3 * tx.i0;
+    const uint8_t* p01 = row0 + 3 * tx.i1;
+    const uint8_t* p10 = row1 + 3 * tx.i0;
+    const uint8_t* p11 = row1 + 3 * tx.i1;
+    uint32_t s[4][3];
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+      s[0][c] = load_u8<kCoherent>(p00 + c);
+      s[1][c] = load_u8<kCoherent>(p01 + c);
+      s[2][c] = load_u8<kCoherent>(p10 + c);
+      s[3][c] = load_u8<kCoherent>(p11 + c);
+    }
+    return blend_bytes(s, tx, Dx, ty, Dy, inv_area);
   }
 
   static FKL_D F3 exec(const Point& pt, const ParamsType& p) {

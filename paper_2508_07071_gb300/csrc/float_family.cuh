@@ -10,6 +10,7 @@
 #include <tuple>
 
 #include "fkl/staged.cuh"
+#include "fkl/tiles.cuh"
 #include "registry.h"
 
 namespace fkl_impl {
@@ -213,8 +214,72 @@ inline bool staged_eligible(const LaunchCtx& c, int V) {
   return true;
 }
 
+// Tile-staged launch of the packed reader (shape.ry == -1): tiles of
+// (shape.tx * V) x shape.ty outputs, each staging its tap rows' column span in
+// shared memory. Eligible when every image's span fits kTileSmemMax bytes.
+constexpr int kTileSmemMax = 48 * 1024;
+
+// Shared bytes per staged row for this launch (0: a span does not fit).
+inline int tile_row_stride(const LaunchCtx& c, int V) {
+  if (c.shape.ty < 1 || c.shape.ty > fkl::kTileMaxRows || c.shape.tx < 1 || c.shape.tx * c.shape.ty > 256) return 0;
+  const int64_t tile_w = int64_t(c.shape.tx) * V;
+  int64_t nb_max = 0;
+  for (int i = 0; i < c.n; ++i) {
+    const auto& p = c.imgs[i];
+    // tap columns of tile_w consecutive outputs span at most
+    // (tile_w - 1) rw / dw + 3 source pixels
+    const int64_t span = ((tile_w - 1) * p.rw + p.dw - 1) / p.dw + 3;
+    nb_max = std::max(nb_max, 3 * span);
+  }
+  const int64_t stride = ((nb_max + 30) / 16 + 1) * 16;
+  return 2 * c.shape.ty * stride <= kTileSmemMax ? static_cast<int>(stride) : 0;
+}
+
+template <class OutT, bool kSplit, bool kSwap, int kTail, int V, int CAP>
+cudaError_t run_tiles_cap(const LaunchCtx& c, int stride) {
+  using RB = fkl::BatchRead<fkl::ResizeU8C3, CAP>;
+  using W = std::conditional_t<kSplit, fkl::WriteSplit<OutT>, fkl::WritePacked<OutT>>;
+  const Spec& s = *c.spec;
+  auto tail = make_tail<kTail>(s);
+  auto cops = [&] {
+    if constexpr (kSwap) {
+      return fkl::prepend(fkl::IOp<fkl::SwapRB<fkl::F3>>{}, tail);
+    } else {
+      return tail;
+    }
+  }();
+  using Cops = decltype(cops);
+  fkl::TileArgs<RB, W, Cops> a;
+  std::memset(&a.rp, 0, sizeof(a.rp));
+  a.rp.count = c.n;
+  std::memcpy(a.rp.p, c.imgs, sizeof(fkl::ResampleParams) * c.n);
+  a.wp = c.out;
+  a.cops = cops;
+  a.H = c.H;
+  a.W_ = c.W;
+  a.row_stride = stride;
+  const int tile_w = c.shape.tx * V;
+  const dim3 grid((c.W + tile_w - 1) / tile_w, (c.H + c.shape.ty - 1) / c.shape.ty, c.n);
+  fkl::tile_resize_kernel<V, RB, W, Cops><<<grid, dim3(c.shape.tx, c.shape.ty, 1), 2 * c.shape.ty * stride,
+                                              c.stream>>>(a);
+  return cudaGetLastError();
+}
+
+template <class OutT, bool kSplit, bool kSwap, int kTail, int V>
+cudaError_t run_tiles(const LaunchCtx& c, int stride) {
+  if (c.n <= kSmallCap) return run_tiles_cap<OutT, kSplit, kSwap, kTail, V, kSmallCap>(c, stride);
+  if (c.n <= kMidCap) return run_tiles_cap<OutT, kSplit, kSwap, kTail, V, kMidCap>(c, stride);
+  return run_tiles_cap<OutT, kSplit, kSwap, kTail, V, kBatchCap>(c, stride);
+}
+
 template <class ROp, class OutT, bool kSplit, bool kSwap, int kTail, int V>
 cudaError_t float_by_ry(const LaunchCtx& c) {
+  if constexpr (std::is_same_v<ROp, fkl::ResizeU8C3> && V <= 4) {
+    if (c.shape.ry == -1) {
+      const int stride = tile_row_stride(c, V);
+      if (stride > 0) return run_tiles<OutT, kSplit, kSwap, kTail, V>(c, stride);
+    }
+  }
   if (c.shape.ry <= 0) {
     if constexpr (std::is_same_v<ROp, fkl::ResizeNV12x2> && kSplit && V % 8 == 0) {
       if (staged_eligible(c, V)) return run_staged<OutT, kSwap, kTail, V>(c);

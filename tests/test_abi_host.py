@@ -131,8 +131,10 @@ def test_launch_shapes(F):
                 assert s[0] in (4, 8, 16) and s[1] * s[2] <= 256 and s[3] in (1, 2)
         assert any(s[3] <= 0 for s in shapes)
         packed = F.fkl_pipeline_create(W.normalize_chain(224, 224, F.FKL_BF16))
-        try:
-            assert all(s[3] > 0 for s in F.fkl_pipeline_shapes(packed))
+        try:  # the packed reader: register shapes and tile-staged shapes (ry = -1, 2 pixels per thread)
+            ps = F.fkl_pipeline_shapes(packed)
+            assert all(s[3] > 0 or (s[3] == -1 and s[0] <= 4 and s[1] * s[2] <= 256) for s in ps)
+            assert any(s[3] == -1 for s in ps)
         finally:
             F.fkl_pipeline_destroy(packed)
         F.fkl_pipeline_set_shape(p, shapes[-1])

@@ -543,7 +543,7 @@ def test_reduce_many_jobs_per_block_against_the_oracle_and_the_write(F, W):
     count is checked against the grid): statistics against the oracle's, the
     extremes equal bit for bit to those of the fused chain's float32 output,
     and the dynamic FP8 codes of sampled frames within 1 ulp."""
-    n = 40
+    n = 48
     frames = synth.nv12_frames(19, n, 720, 1280)
     dev = torch.from_numpy(frames).cuda()
     ins = [F.as_fkl(dev[i], F.FKL_LAYOUT_NV12) for i in range(n)]
@@ -1151,3 +1151,81 @@ def test_per_op_refuses_other_families(F, W):
     with pytest.raises(F.FklError) as ei:
         F.fkl_per_op_workspace_bytes(p.handle, [F.as_fkl(src)], None, F.as_fkl(out, F.FKL_LAYOUT_NHWC))
     assert ei.value.status == F.FKL_ERR_UNSUPPORTED
+
+
+# ------------------------------------------------------------------ tile-staged packed reader (shared memory)
+
+
+def _tile_shapes(F, p):
+    return [s for s in F.fkl_pipeline_shapes(p.handle) if s[3] == -1]
+
+
+@pytest.mark.parametrize("case", ["hf_crops", "upscale", "odd_pitch", "letterbox"])
+def test_tile_staged_reader_equals_register_reader(F, W, case):
+    """The packed reader that stages each tile's tap rows in shared memory
+    (16-byte loads, ends byte by byte) gives the register reader's bytes on
+    every tile shape, and the oracle's values."""
+    if case == "hf_crops":
+        cfg = W.HF
+        src = synth.packed_image(1, cfg["src_h"], cfg["src_w"])
+        rois = synth.crop_rois(1, cfg["n"], cfg["src_w"], cfg["src_h"], cfg["w_range"], cfg["h_range"])
+        ow, oh = cfg["out_w"], cfg["out_h"]
+        ops = W.normalize_chain(ow, oh)
+        t = torch.from_numpy(src).cuda()
+        ins = [t] * len(rois)
+    elif case == "upscale":
+        src = synth.packed_image(34, 30, 41)
+        rois = np.array([[0, 0, 41, 30], [3, 2, 17, 11], [40, 29, 1, 1]], np.int32)
+        ow, oh = 97, 61
+        ops = W.normalize_chain(ow, oh)
+        t = torch.from_numpy(src).cuda()
+        ins = [t] * 3
+    elif case == "odd_pitch":
+        full = synth.packed_image(35, 120, 203)                   # rows of 609 bytes, viewed with a 5-byte gap
+        host = np.zeros((120, 614), np.uint8)
+        host[:, :609] = full.reshape(120, 609)
+        dev = torch.from_numpy(host).cuda()
+        view = torch.as_strided(dev, (120, 203, 3), (614, 3, 1), storage_offset=0)
+        src = full
+        rois = np.array([[0, 0, 203, 120], [1, 1, 200, 117], [77, 13, 101, 99]], np.int32)
+        ow, oh = 64, 48
+        ops = W.normalize_chain(ow, oh)
+        ins = [view] * 3
+    else:
+        src = synth.packed_image(36, 300, 170)
+        rois = None
+        ow, oh = 128, 96
+        ops = [F.read_u8c3(), F.letterbox(ow, oh, 114.0), F.swap_rb(), F.mul(W.INV255), F.write_split(F.FKL_F32)]
+        t = torch.from_numpy(src).cuda()
+        ins = [t] * 2
+    n = len(ins)
+    p = F.Pipeline(ops)
+    shapes = _tile_shapes(F, p)
+    assert shapes
+    base = run_batch(F, ops, ins, rois, (n, 3, oh, ow), "f32", shape=(2, 16, 8, 1))
+    for shape in shapes:
+        got = run_batch(F, ops, ins, rois, (n, 3, oh, ow), "f32", shape=shape)
+        assert torch.equal(got.view(torch.int32), base.view(torch.int32)), (case, shape)
+    if case == "letterbox":
+        want = np.stack([O.split(O.multiply(O.swap_rb(O.letterbox(src.astype(np.float64), ow, oh, 114.0)), 1 / 255))
+                         for _ in range(n)])
+    else:
+        want = O.preprocess_packed_batch([src] * n, rois, ow, oh, swap=True, mul=1 / 255,
+                                         sub=W.IMAGENET_MEAN, div=W.IMAGENET_STD)
+    check_f32(to_numpy(base), want, case)
+
+
+def test_tile_staged_reader_falls_back_when_a_span_is_too_wide(F, W):
+    """A 16384-pixel-wide row shrunk to 128 columns: a tile's tap span does not
+    fit shared memory, so the tile shape runs the register reader (same bytes)."""
+    src = synth.packed_image(37, 24, 16384)
+    ops = W.normalize_chain(128, 12)
+    d = torch.from_numpy(src).cuda()
+    p = F.Pipeline(ops)
+    base = run_batch(F, ops, [d], None, (1, 3, 12, 128), "f32", shape=(2, 16, 8, 1))
+    for shape in _tile_shapes(F, p):
+        got = run_batch(F, ops, [d], None, (1, 3, 12, 128), "f32", shape=shape)
+        assert torch.equal(got.view(torch.int32), base.view(torch.int32)), shape
+    want = O.preprocess_packed(src, (0, 0, 16384, 24), 128, 12, swap=True, mul=1 / 255,
+                               sub=W.IMAGENET_MEAN, div=W.IMAGENET_STD)
+    check_f32(to_numpy(base)[0], want, "16384 -> 128")
