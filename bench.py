@@ -687,7 +687,8 @@ def run_serve(args):
     for rate in [float(x) for x in args.rates.split(",")]:
         arrivals = synth.poisson_arrivals(4, rate, len(reqs))
         for mode, mname in ((F.FKL_SERVE_PERSISTENT, "persistent"), (F.FKL_SERVE_UNFUSED, "unfused_per_request")):
-            srv = F.fkl_server_create(pipe.handle, mode, max_inflight=args.slots, arena_bytes=args.arena_gb << 30)
+            srv = F.fkl_server_create(pipe.handle, mode, max_inflight=args.slots, arena_bytes=args.arena_gb << 30,
+                                      ctas_per_sm=args.ctas_per_sm)
             try:
                 # warm-up: one request through the server
                 rid = F.fkl_server_submit(srv, fk[0])
@@ -991,6 +992,7 @@ def main():
     ap.add_argument("--pool", type=int, default=48, help="serve: distinct host images")
     ap.add_argument("--slots", type=int, default=64, help="serve: request slots")
     ap.add_argument("--arena-gb", type=int, default=16, help="serve: device arena (GiB)")
+    ap.add_argument("--ctas-per-sm", type=int, default=1, help="serve: persistent kernel CTAs per SM")
     ap.add_argument("--out-dtype", default="bf16", choices=["bf16", "f16", "e4m3", "f32"])
     ap.add_argument("--frames", type=int, default=256)
     ap.add_argument("--chain-len", type=int, default=10)

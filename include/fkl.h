@@ -444,18 +444,33 @@ FKL_API void fkl_host_executor_destroy(fkl_host_executor e);
  *
  * Modes:
  *   FKL_SERVE_PERSISTENT  a persistent kernel (up to ctas_per_sm CTAs per SM)
- *                         pulls image tasks from a queue in mapped host
- *                         memory; every image of every admitted request is
- *                         one task; request state lives on the device.
+ *                         pulls tasks from a queue in mapped host memory;
+ *                         a task is a band of 16 output rows of one image.
+ *                         The CTA reads the source rows its band's taps
+ *                         reference straight from the request's pinned host
+ *                         image (16-byte loads over the host link; for a
+ *                         downscale by more than 2, only the two tap rows of
+ *                         each output row -- e.g. at most 448 rows of a
+ *                         2160-row image for 224 output rows -- instead of
+ *                         the whole image) into device memory, then runs the
+ *                         chain on the band. No copy engine and no host
+ *                         round trip sit between admission and the kernel;
+ *                         request completion is counted on the device. Images
+ *                         must be pinned host memory (cudaHostAlloc or
+ *                         cudaHostRegister; anything else is
+ *                         FKL_ERR_INVALID at submit) and stay valid until
+ *                         the request is done; a request holds at most
+ *                         8192 / ceil(H / 16) images.
  *   FKL_SERVE_BATCH       one fused fkl_execute_batch launch per request.
  *   FKL_SERVE_UNFUSED     per request, the unfused one-kernel-per-op form
  *                         (the conventional-library baseline).
  * Admission: requests are admitted in arrival order (FIFO) when one of
  * `max_inflight` slots is free and the first-fit allocator of a device arena
- * of `arena_bytes` finds room for the request's images (copied with tight
- * rows, one contiguous copy per image when the host rows are tight) and
- * outputs. A request that could never fit is
- * refused at submit (FKL_ERR_INVALID).
+ * of `arena_bytes` finds room for the request's device copies of its images
+ * (persistent mode: the staged tap rows; other modes: the whole images,
+ * copied with tight rows, one contiguous copy per image when the host rows
+ * are tight) and outputs. A request that could never fit is refused at
+ * submit (FKL_ERR_INVALID).
  * Waits: the persistent kernel's CTAs stop after `idle_us` microseconds
  * without work (or at destroy); the server relaunches them when work
  * arrives. No device wait is unbounded.
@@ -469,14 +484,19 @@ typedef struct {
   int32_t mode;            /* FKL_SERVE_*                                      */
   int32_t max_inflight;    /* request slots, 1..1024                           */
   size_t arena_bytes;      /* device memory for admitted requests              */
-  int32_t ctas_per_sm;     /* persistent mode: CTAs per SM (1..8)              */
+  int32_t ctas_per_sm;     /* persistent mode: CTAs per SM (1..8); 1 is the
+                              fastest measured (more bands in flight read
+                              more scattered host pages at once: a burst of
+                              1,201 mixed images ran at 47K, 25K and 13K
+                              images/s with 1, 2 and 4)                      */
   int32_t idle_us;         /* persistent mode: CTA idle timeout                */
 } fkl_server_config;
 
 typedef struct {
   double t_submit;         /* submit() called                                  */
   double t_admit;          /* slot and memory granted, copies enqueued         */
-  double t_ready;          /* copies to the device complete, work published    */
+  double t_ready;          /* work published to the kernel (persistent mode:
+                              at once; other modes: copies complete)          */
   double t_done;           /* every output image written                       */
   int32_t n_images;
   int32_t state;           /* 0 queued, 1 copying, 2 running, 3 done           */
@@ -494,8 +514,10 @@ typedef struct fkl_server_s* fkl_server;
 /* Create: allocates the arena and control blocks, starts the host thread.
  * The pipeline must outlive the server. */
 FKL_API fkl_status fkl_server_create(fkl_pipeline p, const fkl_server_config* cfg, fkl_server* out);
-/* Submit n host images (HWC u8; pinned memory for asynchronous copies). The
- * images must stay valid until the request's t_ready. Returns at once. */
+/* Submit n host images (HWC u8). Persistent mode: pinned host memory, valid
+ * until the request is done (the kernel reads it). Other modes: pinned memory
+ * for asynchronous copies, valid until the request's t_ready. Returns at
+ * once. */
 FKL_API fkl_status fkl_server_submit(fkl_server s, int32_t n, const fkl_tensor* images,
                                      uint64_t* request_id);
 /* Non-blocking: *done = 1 once every output of the request is written;

@@ -1,12 +1,18 @@
 // Serving runtime (include/fkl.h, fkl_server_*): continuous batching of
 // preprocessing requests with admission by free device memory.
 //
-// Persistent mode: a persistent kernel whose CTAs claim image tasks from a
-// ring in mapped host memory (tail written by the host with release order,
-// head claimed on the device with compare-and-swap), run the chain's Ops on
-// the image, and count the request down; the CTA that finishes a request's
-// last image publishes its sequence number to the host. Every device wait is
-// bounded by an idle timeout on the global timer and by a stop flag.
+// Persistent mode: a persistent kernel whose CTAs claim tasks from a ring in
+// mapped host memory (tail written by the host with release order, head
+// claimed on the device with compare-and-swap). A task is a band of 16
+// output rows of one image: the CTA first gathers the source rows that band's
+// bilinear taps reference straight from the request's pinned host image into
+// device memory (16-byte loads over the host link; for a downscale by more
+// than 2 only the two tap rows of each output row, at most 2 x 224 rows of a
+// 224-row output, instead of the whole image), then runs the chain's Ops on
+// the band. Each request slot has a device counter of finished tasks that only
+// grows; the CTA that brings it to the request's target publishes the
+// request's sequence number to the host. Every device wait is bounded by an
+// idle timeout on the global timer and by a stop flag.
 #include <time.h>
 
 #include <algorithm>
@@ -35,14 +41,27 @@ constexpr int kQueue = 8192;    // task ring entries
 constexpr int kMaxSlots = 1024;  // request slots
 constexpr int kV = 8;            // output pixels per thread and item
 constexpr int kThreads = 256;
+constexpr int kBand = 16;        // output rows per task
+constexpr int kMaxStaged = 2 * kBand + 2;  // staged source rows of one band (bound)
+constexpr int32_t kRowPairs = 1 << 4;      // flags: staged rows 2 ly, 2 ly + 1 are output row ly's taps
 
-struct Task {  // one image of one request
+// One band of one image of one request. rp describes the staged copy of the
+// image's crop window in device memory: rp.src its first staged row, rp.pitch
+// the staged row pitch, rp.uv (as int32) the staged rows' byte offsets (a
+// row's first byte sits `offset` bytes into it, the host row's address mod
+// 16), rp.flags & kRowPairs the staging mode; the rest is the placement of
+// image_params (rx = ry = 0: the window starts the staged rows).
+struct Task {
   fkl::ResampleParams rp;
-  uint8_t* out;     // this image's first output plane
-  int64_t plane;    // bytes between output planes
-  uint64_t seq;     // request sequence number (its completion value)
-  int32_t slot;     // request slot
-  int32_t _pad[9];
+  const uint8_t* host;  // device address of the host image's window origin
+  int64_t host_pitch;   // bytes between host rows
+  uint8_t* out;         // this image's first output plane
+  int64_t plane;        // bytes between output planes
+  uint64_t seq;         // request sequence number (its completion value)
+  uint64_t target;      // slot counter value once every task of the request is done
+  int32_t slot;         // request slot
+  int32_t band;         // first output row = band * kBand
+  int32_t _pad[2];
 };
 static_assert(sizeof(Task) == 128, "task ring entry");
 
@@ -56,8 +75,8 @@ struct HostCtl {  // mapped pinned memory
 };
 
 struct DevCtl {  // device memory
-  unsigned long long head;  // tasks claimed
-  int remaining[kMaxSlots];  // images left per slot
+  unsigned long long head;               // tasks claimed
+  unsigned long long finished[kMaxSlots];  // tasks finished per slot, all requests (never reset)
 };
 
 struct KArgs {
@@ -78,45 +97,159 @@ __device__ __forceinline__ unsigned long long globaltimer_ns() {
   return t;
 }
 
-// Thread 0: claim the next task into `dst`; 1 = claimed, 0 = stop or idle.
-__device__ int claim(const KArgs& a, Task& dst) {
+// Thread 0: claim the next task; its ring position in *slot_out. 1 =
+// claimed, 0 = stop or idle. (The CTA then copies the task, see copy_task.)
+__device__ int claim(const KArgs& a, unsigned long long* slot_out) {
   cuda::atomic_ref<unsigned long long, cuda::thread_scope_device> head(a.dc->head);
   cuda::atomic_ref<unsigned long long, cuda::thread_scope_system> tail(a.hc->tail);
   cuda::atomic_ref<int, cuda::thread_scope_system> stop(a.hc->stop);
   const unsigned long long t0 = globaltimer_ns();
-  unsigned ns = 128;
+  unsigned ns = 1024;
   for (;;) {
     if (stop.load(cuda::memory_order_relaxed)) return 0;
     unsigned long long h = head.load(cuda::memory_order_relaxed);
     const unsigned long long t = tail.load(cuda::memory_order_acquire);
     if (h < t) {
       if (head.compare_exchange_strong(h, h + 1, cuda::memory_order_acq_rel)) {
-        const volatile unsigned long long* src =
-            reinterpret_cast<const volatile unsigned long long*>(&a.hc->tasks[h % kQueue]);
-        unsigned long long* d = reinterpret_cast<unsigned long long*>(&dst);
-#pragma unroll
-        for (int i = 0; i < static_cast<int>(sizeof(Task) / 8); ++i) d[i] = src[i];
+        *slot_out = h;
         return 1;
       }
       continue;
     }
     if (globaltimer_ns() - t0 > a.idle_ns) return 0;
     __nanosleep(ns);
-    ns = min(ns * 2, 16384u);
+    ns = min(ns * 2, 65536u);
   }
 }
 
+// The CTA's first 16 threads copy a claimed task (16 words of 8 bytes) from
+// the ring in mapped host memory into shared memory in parallel, one word
+// each: one round trip over the host link instead of sixteen. The ring entry
+// was written before the host's release store of `tail`, which the claim
+// read with acquire order, and is not rewritten before the task completes.
+__device__ void copy_task(const KArgs& a, unsigned long long h, Task& dst) {
+  if (threadIdx.x < sizeof(Task) / 8) {
+    const volatile unsigned long long* src =
+        reinterpret_cast<const volatile unsigned long long*>(&a.hc->tasks[h % kQueue]);
+    reinterpret_cast<unsigned long long*>(&dst)[threadIdx.x] = src[threadIdx.x];
+  }
+}
+
+// The source row that staged row t of a band holds (staging index t):
+// kRowPairs: t = 2 ly + k holds tap row k of output row ly; otherwise staged
+// rows are the window's rows, t = source row.
+__device__ int staged_source_row(const fkl::ResampleParams& q, int t) {
+  if (q.flags & kRowPairs) {
+    const fkl::AxisTap ty = fkl::AxisWalker(t >> 1, q.rh, q.dh).tap();
+    return (t & 1) ? ty.i1 : ty.i0;
+  }
+  return t;
+}
+
+// Gathers the staged rows of output rows [ly0, ly1) of the window (all
+// threads of the CTA): each row's 3 rw bytes are copied from the host image
+// with 16-byte loads of the aligned chunks wholly inside the row and single
+// bytes at its two ends (nothing outside the row is read); staged row t keeps
+// the host row's alignment: byte b of the row sits at t * pitch + off + b,
+// off = (host row address) mod 16, recorded in the offset table.
+__device__ void gather_band(const Task& task, int ly0, int ly1, int* s_rows, int* s_src, int* s_off) {
+  const fkl::ResampleParams& q = task.rp;
+  const bool pairs = q.flags & kRowPairs;
+  int first, last;  // staged rows of the band: [first, last]
+  if (pairs) {
+    first = 2 * ly0;
+    last = 2 * ly1 - 1;
+  } else {
+    first = fkl::AxisWalker(ly0, q.rh, q.dh).tap().i0;
+    last = fkl::AxisWalker(ly1 - 1, q.rh, q.dh).tap().i1;
+  }
+  const int rows = last - first + 1;  // <= kMaxStaged for a downscale band; full windows may need more
+  const int nb = 3 * q.rw;
+  int32_t* offsets = const_cast<int32_t*>(reinterpret_cast<const int32_t*>(q.uv));
+  uint8_t* stage = const_cast<uint8_t*>(q.src);
+  for (int base = 0; base < rows; base += kMaxStaged) {
+    const int k = min(kMaxStaged, rows - base);
+    __syncthreads();  // the previous round's table is no longer read
+    if (threadIdx.x < k) {
+      const int t = first + base + threadIdx.x;
+      const int src = staged_source_row(q, t);
+      const uint8_t* g = task.host + static_cast<int64_t>(src) * task.host_pitch;
+      s_rows[threadIdx.x] = t;
+      s_src[threadIdx.x] = src;
+      s_off[threadIdx.x] = static_cast<int>(reinterpret_cast<uintptr_t>(g) & 15);
+      offsets[t] = s_off[threadIdx.x];
+    }
+    __syncthreads();
+    const int chunks = (nb + 30) / 16 + 1;  // per row, whatever its offset
+    // the chunks wholly inside a row: four 16-byte loads in flight per thread
+    // before their stores (the host link's latency is paid once per four)
+    constexpr int kU = 4;
+    for (int i = threadIdx.x; i < k * chunks; i += kU * blockDim.x) {
+      uint4 v[kU];
+      uint8_t* d[kU];
+#pragma unroll
+      for (int u = 0; u < kU; ++u) {
+        d[u] = nullptr;
+        const int j = i + u * blockDim.x;
+        if (j >= k * chunks) continue;
+        const int r = j / chunks, c = j - r * chunks;
+        const int lo = 16 * c - s_off[r];  // row byte of the chunk's first byte
+        if (lo < 0 || lo + 16 > nb) continue;
+        d[u] = stage + static_cast<int64_t>(s_rows[r]) * q.pitch + 16 * c;
+        v[u] = __ldcs(reinterpret_cast<const uint4*>(task.host + static_cast<int64_t>(s_src[r]) * task.host_pitch + lo));
+      }
+#pragma unroll
+      for (int u = 0; u < kU; ++u)
+        if (d[u]) __stcg(reinterpret_cast<uint4*>(d[u]), v[u]);
+    }
+    // the partial chunks at the two ends of each row, byte by byte
+    for (int i = threadIdx.x; i < k * 32; i += blockDim.x) {
+      const int r = i / 32, e = i - r * 32;
+      const int off = s_off[r];
+      const int c = e < 16 ? 0 : (off + nb - 1) / 16;  // first or last chunk of the row
+      if (e >= 16 && c == 0) continue;                 // a one-chunk row: done with e < 16
+      const int lo = 16 * c - off;
+      if (lo >= 0 && lo + 16 <= nb) continue;          // a whole chunk: copied above
+      const int b = lo + (e & 15);
+      if (b < 0 || b >= nb) continue;
+      stage[static_cast<int64_t>(s_rows[r]) * q.pitch + off + b] =
+          __ldcs(task.host + static_cast<int64_t>(s_src[r]) * task.host_pitch + b);
+    }
+  }
+  __threadfence_block();
+  __syncthreads();
+}
+
+// The bilinear value of window pixel (lx, ly) from the staged rows (the
+// integer blend of ResizeU8C3T::blend_bytes: the fused reader's bits).
+__device__ fkl::F3 staged_pixel(const fkl::ResampleParams& q, const fkl::AxisTap& tx, const fkl::AxisTap& ty, int ly) {
+  const bool pairs = q.flags & kRowPairs;
+  const int t0 = pairs ? 2 * ly : ty.i0, t1 = pairs ? 2 * ly + 1 : ty.i1;
+  const int32_t* offsets = reinterpret_cast<const int32_t*>(q.uv);
+  const uint8_t* r0 = q.src + static_cast<int64_t>(t0) * q.pitch + __ldcg(offsets + t0);
+  const uint8_t* r1 = q.src + static_cast<int64_t>(t1) * q.pitch + __ldcg(offsets + t1);
+  uint32_t b[4][3];
+#pragma unroll
+  for (int c = 0; c < 3; ++c) {
+    b[0][c] = __ldcg(r0 + 3 * tx.i0 + c);
+    b[1][c] = __ldcg(r0 + 3 * tx.i1 + c);
+    b[2][c] = __ldcg(r1 + 3 * tx.i0 + c);
+    b[3][c] = __ldcg(r1 + 3 * tx.i1 + c);
+  }
+  return fkl::ResizeU8C3::blend_bytes(b, tx, 2 * q.dw, ty, 2 * q.dh, q.inv_area);
+}
+
 template <bool kSwap, class OutT>
-__global__ void __launch_bounds__(kThreads) serve_kernel(const __grid_constant__ KArgs a) {
-  using R = fkl::ResizeU8C3T<true>;  // L2-coherent loads: the arena is reused while we run
+__global__ void __launch_bounds__(kThreads, 4) serve_kernel(const __grid_constant__ KArgs a) {
   using Wr = fkl::WriteSplit<OutT>;
   __shared__ Task task;
   __shared__ int cmd;
+  __shared__ unsigned long long claimed;
+  __shared__ int s_rows[kMaxStaged], s_src[kMaxStaged], s_off[kMaxStaged];
   const int cols = (a.W + kV - 1) / kV;
-  const int items = cols * a.H;
   for (;;) {
     if (threadIdx.x == 0) {
-      int c = claim(a, task);
+      int c = claim(a, &claimed);
       while (c == 0) {
         // Leaving: the last CTA re-checks the ring after its decrement, so a
         // task published while it was deciding is never stranded (either it
@@ -130,12 +263,19 @@ __global__ void __launch_bounds__(kThreads) serve_kernel(const __grid_constant__
         cuda::atomic_ref<unsigned long long, cuda::thread_scope_system> tail(a.hc->tail);
         if (head.load(cuda::memory_order_relaxed) >= tail.load(cuda::memory_order_acquire)) break;
         active.fetch_add(1, cuda::memory_order_acq_rel);
-        c = claim(a, task);
+        c = claim(a, &claimed);
       }
       cmd = c;
     }
     __syncthreads();
     if (cmd == 0) return;
+    copy_task(a, claimed, task);
+    __syncthreads();
+    const fkl::ResampleParams& q = task.rp;
+    const int y0 = task.band * kBand, y1 = min(y0 + kBand, a.H);
+    // the band's rows inside the placed window
+    const int ly0 = max(y0 - q.oy, 0), ly1 = min(y1 - q.oy, q.dh);
+    if (ly0 < ly1) gather_band(task, ly0, ly1, s_rows, s_src, s_off);
     fkl::OutParams wp;
     wp.base = task.out;
     wp.img = 0;
@@ -144,20 +284,26 @@ __global__ void __launch_bounds__(kThreads) serve_kernel(const __grid_constant__
     wp.scale_inv = a.scale_inv;
     wp.aligned = a.aligned;
     wp.scale_inv_dev = nullptr;
+    const int items = cols * (y1 - y0);
     for (int it = threadIdx.x; it < items; it += blockDim.x) {
-      const int y = it / cols;
-      const int x0 = (it - y * cols) * kV;
+      const int y = y0 + it / cols;
+      const int x0 = (it % cols) * kV;
       const int n = min(kV, a.W - x0);
-      fkl::F3 in[kV];
-      if (n == kV) {
-        R::template exec_span<kV>(fkl::Point{x0, y, 0}, task.rp, in);
-      } else {
-        for (int k = 0; k < n; ++k) in[k] = R::exec(fkl::Point{x0 + k, y, 0}, task.rp);
-      }
+      const int ly = y - q.oy;
+      const bool row_in = ly >= 0 && ly < q.dh;
+      fkl::AxisTap ty{0, 0, 0};
+      if (row_in) ty = fkl::AxisWalker(ly, q.rh, q.dh).tap();
+      const int lx0 = x0 - q.ox;
+      fkl::AxisWalker wx(max(lx0, 0), q.rw, q.dw);
       fkl::F3 o[kV];
 #pragma unroll
       for (int k = 0; k < kV; ++k) {
-        fkl::F3 v = in[k];
+        const int lx = lx0 + k;
+        fkl::F3 v{{q.pad, q.pad, q.pad}};
+        if (k < n && row_in && lx >= 0 && lx < q.dw) {
+          v = staged_pixel(q, wx.tap(), ty, ly);
+          wx.next();
+        }
         if constexpr (kSwap) v = fkl::SwapRB<fkl::F3>::exec(v);
         v = fkl::Mul3::exec(v, a.mul);
         v = fkl::Sub3::exec(v, a.sub);
@@ -168,8 +314,8 @@ __global__ void __launch_bounds__(kThreads) serve_kernel(const __grid_constant__
     __threadfence();
     __syncthreads();
     if (threadIdx.x == 0) {
-      cuda::atomic_ref<int, cuda::thread_scope_device> rem(a.dc->remaining[task.slot]);
-      if (rem.fetch_sub(1, cuda::memory_order_acq_rel) == 1) {
+      cuda::atomic_ref<unsigned long long, cuda::thread_scope_device> fin(a.dc->finished[task.slot]);
+      if (fin.fetch_add(1, cuda::memory_order_acq_rel) + 1 == task.target) {
         cuda::atomic_thread_fence(cuda::memory_order_seq_cst, cuda::thread_scope_system);
         cuda::atomic_ref<unsigned long long, cuda::thread_scope_system> done(a.hc->done[task.slot]);
         done.store(task.seq, cuda::memory_order_release);
@@ -257,7 +403,9 @@ struct Request {
   uint64_t id = 0, seq = 0;
   int n = 0, slot = -1, state = 0;
   std::vector<fkl_tensor> host;
+  std::vector<const uint8_t*> window;  // persistent mode: device address of each host window's origin
   std::vector<fkl::ResampleParams> rp;
+  uint64_t ntasks = 0, target = 0;     // persistent mode: band tasks, slot counter at completion
   size_t off = 0, len = 0, in_bytes = 0;
   uint64_t first_task = 0;
   double t_submit = 0, t_admit = 0, t_ready = 0, t_done = 0;
@@ -282,7 +430,8 @@ struct fkl_server_s {
   HostCtl* hc = nullptr;
   HostCtl* hc_dev = nullptr;
   DevCtl* dc = nullptr;
-  int* rem_staging = nullptr;  // pinned, one int per slot
+  std::vector<uint64_t> slot_tasks;  // persistent mode: tasks ever assigned to each slot
+  int bands = 0;                     // tasks per image (output rows / kBand, rounded up)
   uint8_t* ws[2] = {nullptr, nullptr};  // unfused-mode workspace per copy stream
   size_t ws_bytes = 0;
   KernelFn kernel = nullptr;
@@ -335,8 +484,80 @@ void ensure_kernel(fkl_server_s* s) {
   }
 }
 
+// The source window and placement of image i of a request.
+fkl::ResampleParams window_params(const fkl_server_s* s, const fkl_tensor& h) {
+  fkl::ResampleParams p;
+  std::memset(&p, 0, sizeof(p));
+  const Spec& sp = s->p->spec;
+  p.rw = sp.has_crop ? sp.crop[2] : static_cast<int32_t>(h.dims[1]);
+  p.rh = sp.has_crop ? sp.crop[3] : static_cast<int32_t>(h.dims[0]);
+  place(sp, s->W, s->H, p);
+  return p;
+}
+
+// Persistent mode's device memory for one image: the staged rows (kRowPairs:
+// two per window row of the output, when that is fewer than the window's
+// rows) with room for their host alignment, then their offset table.
+struct StagedLayout {
+  int rows;
+  int64_t pitch, rows_bytes, bytes;
+  bool pairs;
+};
+StagedLayout staged_layout(const fkl::ResampleParams& p) {
+  StagedLayout L;
+  L.pairs = p.rh > 2 * p.dh;
+  L.rows = L.pairs ? 2 * p.dh : p.rh;
+  L.pitch = static_cast<int64_t>(up(static_cast<size_t>(3) * p.rw + 32, 16));
+  L.rows_bytes = static_cast<int64_t>(up(static_cast<size_t>(L.rows * L.pitch), 256));
+  L.bytes = L.rows_bytes + static_cast<int64_t>(up(static_cast<size_t>(L.rows) * 4, 256));
+  return L;
+}
+
+// Persistent mode: the arena holds each image's staged rows and the outputs;
+// nothing is copied here -- the kernel gathers each band's rows from the
+// pinned host image itself.
+bool admit_persistent(fkl_server_s* s, Request& r) {
+  std::vector<StagedLayout> lay(r.n);
+  std::vector<fkl::ResampleParams> wp(r.n);
+  size_t in_bytes = 0;
+  for (int i = 0; i < r.n; ++i) {
+    wp[i] = window_params(s, r.host[i]);
+    lay[i] = staged_layout(wp[i]);
+    in_bytes += static_cast<size_t>(lay[i].bytes);
+  }
+  const size_t len = in_bytes + r.n * s->out_img;
+  size_t off = 0;
+  if (!s->arena->alloc(len, off)) return false;
+  r.slot = s->free_slots.back();
+  s->free_slots.pop_back();
+  r.off = off;
+  r.len = len;
+  r.in_bytes = in_bytes;
+  r.seq = s->next_seq++;
+  uint8_t* base = s->arena_base + off;
+  r.rp.resize(r.n);
+  size_t at = 0;
+  for (int i = 0; i < r.n; ++i) {
+    fkl::ResampleParams& p = r.rp[i];
+    p = wp[i];
+    p.src = base + at;
+    p.uv = base + at + lay[i].rows_bytes;  // the staged rows' offset table (int32)
+    p.pitch = static_cast<int32_t>(lay[i].pitch);
+    p.flags = lay[i].pairs ? kRowPairs : 0;
+    at += static_cast<size_t>(lay[i].bytes);
+  }
+  r.ntasks = static_cast<uint64_t>(r.n) * s->bands;
+  s->slot_tasks[r.slot] += r.ntasks;
+  r.target = s->slot_tasks[r.slot];
+  r.state = 1;
+  r.t_admit = now_s();
+  s->stats.admitted++;
+  return true;
+}
+
 bool admit(fkl_server_s* s, Request& r) {
   if (s->free_slots.empty()) return false;
+  if (s->cfg.mode == FKL_SERVE_PERSISTENT) return admit_persistent(s, r);
   // layout: images at their tight row size (one contiguous copy each when
   // the host rows are tight too), 256-byte aligned, then the outputs
   size_t in_bytes = 0;
@@ -381,13 +602,8 @@ bool admit(fkl_server_s* s, Request& r) {
     dev_in[i].data = base + offs[i];
     dev_in[i].pitch_bytes = dp;
   }
-  if (ce == cudaSuccess && s->cfg.mode == FKL_SERVE_PERSISTENT) {
-    s->rem_staging[r.slot] = r.n;
-    ce = cudaMemcpyAsync(&s->dc->remaining[r.slot], &s->rem_staging[r.slot], sizeof(int), cudaMemcpyHostToDevice,
-                         cs);
-  }
   if (ce == cudaSuccess) ce = cudaEventRecord(r.ev_copy, cs);
-  if (ce == cudaSuccess && s->cfg.mode != FKL_SERVE_PERSISTENT) {
+  if (ce == cudaSuccess) {
     fkl_tensor out{};
     out.data = base + in_bytes;
     out.dims[0] = r.n;
@@ -412,22 +628,32 @@ bool admit(fkl_server_s* s, Request& r) {
   return true;
 }
 
+// Writes a request's band tasks into the ring (persistent mode); false when
+// the ring has no room for them yet.
 bool publish(fkl_server_s* s, Request& r) {
   uint64_t oldest = s->tail;
   for (auto& kv : s->reqs)
     if (kv.second.state == 2) oldest = std::min(oldest, kv.second.first_task);
-  if (s->tail + r.n - oldest > static_cast<uint64_t>(kQueue)) return false;  // ring full
+  if (s->tail + r.ntasks - oldest > static_cast<uint64_t>(kQueue)) return false;  // ring full
   uint8_t* out = s->arena_base + r.off + r.in_bytes;
   r.first_task = s->tail;
+  uint64_t k = s->tail;
   for (int i = 0; i < r.n; ++i) {
-    Task& t = s->hc->tasks[(s->tail + i) % kQueue];
-    t.rp = r.rp[i];
-    t.out = out + i * s->out_img;
-    t.plane = static_cast<int64_t>(s->H) * s->out_pitch;
-    t.seq = r.seq;
-    t.slot = r.slot;
+    const int64_t hp = r.host[i].pitch_bytes ? r.host[i].pitch_bytes : r.host[i].dims[1] * 3;
+    for (int b = 0; b < s->bands; ++b, ++k) {
+      Task& t = s->hc->tasks[k % kQueue];
+      t.rp = r.rp[i];
+      t.host = r.window[i];
+      t.host_pitch = hp;
+      t.out = out + i * s->out_img;
+      t.plane = static_cast<int64_t>(s->H) * s->out_pitch;
+      t.seq = r.seq;
+      t.target = r.target;
+      t.slot = r.slot;
+      t.band = b;
+    }
   }
-  s->tail += r.n;
+  s->tail = k;
   cuda::atomic_ref<unsigned long long, cuda::thread_scope_system> tail(s->hc->tail);
   tail.store(s->tail, cuda::memory_order_release);
   ensure_kernel(s);
@@ -446,7 +672,7 @@ void server_loop(fkl_server_s* s) {
     int busy = 0;
     for (auto& kv : s->reqs) {
       Request& r = kv.second;
-      if (r.state == 1 && cudaEventQuery(r.ev_copy) == cudaSuccess) {
+      if (r.state == 1 && (s->cfg.mode == FKL_SERVE_PERSISTENT || cudaEventQuery(r.ev_copy) == cudaSuccess)) {
         if (s->cfg.mode == FKL_SERVE_PERSISTENT) {
           if (!publish(s, r)) continue;
         }
@@ -516,7 +742,6 @@ void teardown(fkl_server_s* s) {
   for (uint8_t* w : s->ws)
     if (w) cudaFree(w);
   if (s->hc) cudaFreeHost(s->hc);
-  if (s->rem_staging) cudaFreeHost(s->rem_staging);
   delete s->arena;
   delete s;
 }
@@ -556,7 +781,6 @@ fkl_status fkl_server_create(fkl_pipeline p, const fkl_server_config* cfg, fkl_s
     std::memset(s->hc, 0, sizeof(HostCtl));
     ce = cudaHostGetDevicePointer(reinterpret_cast<void**>(&s->hc_dev), s->hc, 0);
   }
-  if (ce == cudaSuccess) ce = cudaHostAlloc(reinterpret_cast<void**>(&s->rem_staging), kMaxSlots * sizeof(int), 0);
   if (ce == cudaSuccess && cfg->mode == FKL_SERVE_UNFUSED) {
     s->ws_bytes = 2 * up(static_cast<size_t>(s->H) * s->W * 12, 256);
     for (int i = 0; i < 2 && ce == cudaSuccess; ++i) ce = cudaMalloc(reinterpret_cast<void**>(&s->ws[i]), s->ws_bytes);
@@ -573,6 +797,8 @@ fkl_status fkl_server_create(fkl_pipeline p, const fkl_server_config* cfg, fkl_s
   }
   s->arena = new Arena(cfg->arena_bytes);
   for (int i = cfg->max_inflight - 1; i >= 0; --i) s->free_slots.push_back(i);
+  s->slot_tasks.assign(cfg->max_inflight, 0);
+  s->bands = (s->H + kBand - 1) / kBand;
   s->grid = sm_count() * cfg->ctas_per_sm;
   KArgs& k = s->kargs;
   k.hc = s->hc_dev;
@@ -600,6 +826,10 @@ fkl_status fkl_server_submit(fkl_server s, int32_t n, const fkl_tensor* images, 
   r.host.assign(images, images + n);
   size_t need = 0;
   const Spec& sp = s->p->spec;
+  const bool persistent = s->cfg.mode == FKL_SERVE_PERSISTENT;
+  if (persistent && static_cast<int64_t>(n) * s->bands > kQueue)
+    return sfail(FKL_ERR_INVALID, "a request may hold at most %d images (%d tasks of %d output rows each)",
+                 kQueue / s->bands, s->bands, kBand);
   for (int i = 0; i < n; ++i) {
     const fkl_tensor& t = images[i];
     if (!t.data || t.layout != FKL_LAYOUT_HWC || t.dtype != FKL_U8 || t.dims[2] != 3 || t.dims[0] < 1 ||
@@ -608,7 +838,22 @@ fkl_status fkl_server_submit(fkl_server s, int32_t n, const fkl_tensor* images, 
     if (t.pitch_bytes && t.pitch_bytes < t.dims[1] * 3) return sfail(FKL_ERR_INVALID, "image %d: pitch too small", i);
     if (sp.has_crop && (sp.crop[0] + int64_t(sp.crop[2]) > t.dims[1] || sp.crop[1] + int64_t(sp.crop[3]) > t.dims[0]))
       return sfail(FKL_ERR_INVALID, "image %d: the chain's crop does not fit", i);
-    need += up(static_cast<size_t>(t.dims[0]) * t.dims[1] * 3, 256);
+    if (persistent) {
+      // the kernel reads the image itself: it must be pinned (device-accessible) host memory
+      cudaPointerAttributes at;
+      if (cudaPointerGetAttributes(&at, t.data) != cudaSuccess || at.type != cudaMemoryTypeHost ||
+          !at.devicePointer) {
+        cudaGetLastError();
+        return sfail(FKL_ERR_INVALID, "image %d: persistent servers read pinned host memory (cudaHostAlloc or "
+                     "cudaHostRegister)", i);
+      }
+      const int64_t hp = t.pitch_bytes ? t.pitch_bytes : t.dims[1] * 3;
+      const int64_t x = sp.has_crop ? sp.crop[0] : 0, y = sp.has_crop ? sp.crop[1] : 0;
+      r.window.push_back(static_cast<const uint8_t*>(at.devicePointer) + y * hp + 3 * x);
+      need += static_cast<size_t>(staged_layout(window_params(s, t)).bytes);
+    } else {
+      need += up(static_cast<size_t>(t.dims[0]) * t.dims[1] * 3, 256);
+    }
   }
   need += n * s->out_img;
   if (up(need, 256) > s->arena->size())

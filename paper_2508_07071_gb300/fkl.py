@@ -597,7 +597,7 @@ def fkl_execute_batch_host(e: int, ins: Sequence[fkl_tensor], rois, out: fkl_ten
 
 
 def fkl_server_create(p: int, mode: int = FKL_SERVE_PERSISTENT, max_inflight: int = 64,
-                      arena_bytes: int = 4 << 30, ctas_per_sm: int = 4, idle_us: int = 200000) -> int:
+                      arena_bytes: int = 4 << 30, ctas_per_sm: int = 1, idle_us: int = 200000) -> int:
     cfg = fkl_server_config(mode, max_inflight, arena_bytes, ctas_per_sm, idle_us)
     h = ctypes.c_void_p()
     _check(_lib.fkl_server_create(p, ctypes.byref(cfg), ctypes.byref(h)))

@@ -124,8 +124,8 @@ def test_admission_by_device_memory(F, pool):
             assert torch.equal(o.view(torch.int16), outs[0].view(torch.int16))
         st = F.fkl_server_get_stats(srv)
         assert st.completed == 6 and st.arena_peak_bytes <= int(one * 2.5) + (1 << 20)
-        with pytest.raises(F.FklError):  # could never fit
-            F.fkl_server_submit(srv, [F.as_fkl(pool[i]) for i in big] * 3)
+        with pytest.raises(F.FklError):  # could never fit (even as staged tap rows: 24 images)
+            F.fkl_server_submit(srv, [F.as_fkl(pool[i]) for i in big] * 8)
     finally:
         F.fkl_server_destroy(srv)
 
@@ -208,3 +208,20 @@ def test_requests_overlap_on_the_device(F, pool):
     assert overlapped, [(x.t_admit, x.t_ready, x.t_done) for x in infos]
     # FIFO admission: no request is admitted before one submitted earlier
     assert all(infos[k].t_admit <= infos[k + 1].t_admit for k in range(len(infos) - 1))
+
+
+def test_persistent_mode_refuses_pageable_images(F, pool):
+    """The persistent kernel reads the host images itself: pageable memory is
+    refused at submit, pinned memory accepted."""
+    p = pipeline(F)
+    srv = F.fkl_server_create(p.handle, F.FKL_SERVE_PERSISTENT, max_inflight=4, arena_bytes=1 << 28)
+    try:
+        pageable = torch.from_numpy(synth.packed_image(7, 300, 400))
+        with pytest.raises(F.FklError) as ei:
+            F.fkl_server_submit(srv, [F.as_fkl(pageable)])
+        assert ei.value.status == F.FKL_ERR_INVALID
+        rid = F.fkl_server_submit(srv, [F.as_fkl(pool[0])])
+        F.fkl_server_wait(srv, rid, 30000)
+        F.fkl_server_release(srv, rid)
+    finally:
+        F.fkl_server_destroy(srv)
