@@ -47,7 +47,7 @@ def source_hash(files: list[str] | None = None) -> str:
 # (core.cuh also fixes the parameter-table capacity, a template argument of
 # the kernels). A traffic entry hashes these plus its translation unit;
 # host-only sources (registry.h, api.cu, the other families) are not part of it.
-DEVICE_HEADERS = ["fkl/core.cuh", "fkl/ops.cuh", "fkl/dpp.cuh", "fkl/staged.cuh", "float_family.cuh"]
+DEVICE_HEADERS = ["fkl/core.cuh", "fkl/ops.cuh", "fkl/dpp.cuh", "fkl/staged.cuh", "fkl/tiles.cuh", "float_family.cuh"]
 
 
 def entry_hash(entry: dict) -> str:
