@@ -459,7 +459,58 @@ def secondary_configs(args, F, W, synth, metrics, torch, stream, peak, peak_kind
                           "frac": out[key]["roofline"]["frac"]}), file=sys.stderr, flush=True)
         del wl
         torch.cuda.empty_cache()
+    out["nv12_256_letterbox_fp8_dynamic_scale"] = dynamic_fp8(args, F, W, synth, torch, stream, peak)
+    print(json.dumps({"secondary": "nv12_256_letterbox_fp8_dynamic_scale",
+                      "ms": out["nv12_256_letterbox_fp8_dynamic_scale"]["ms_per_step"]}), file=sys.stderr, flush=True)
+    if args.serve_requests > 0:
+        _, _, pipe, fk = serve_setup(F, W, synth, torch, args.pool, args.serve_requests)
+        sv = {"workload": f"Poisson requests at 1000 req/s, {args.serve_requests} requests of 1-64 pinned u8 BGR "
+                          f"images 320-3840 x 240-2160 -> 224x224 RGB normalised planar f16"}
+        for mode, mname in ((F.FKL_SERVE_PERSISTENT, "persistent"), (F.FKL_SERVE_UNFUSED, "unfused_per_request")):
+            sv[mname] = serve_rate(F, synth, pipe, fk, 1000.0, mode, args.slots, args.arena_gb, args.ctas_per_sm)
+        out["serving_1000rps"] = sv
+        print(json.dumps({"secondary": "serving_1000rps", "images_per_s": sv["persistent"]["images_per_s"]}),
+              file=sys.stderr, flush=True)
     return out
+
+
+def dynamic_fp8(args, F, W, synth, torch, stream, peak):
+    """ReduceDPP over the 256-frame NV12 batch (the statistics and the FP8
+    scale in device memory), then the FP8 write with that scale: the dynamic
+    per-tensor scaling step, CUDA events per step, no L2 flush (354 MB of
+    frames are larger than L2)."""
+    cfg = W.NV12
+    n, h, w, side = args.frames, cfg["h"], cfg["w"], cfg["out"]
+    frames = torch.from_numpy(synth.nv12_frames(3, n, h, w)).cuda()
+    ins = [F.as_fkl(frames[i], F.FKL_LAYOUT_NV12) for i in range(n)]
+    p = F.Pipeline(W.nv12_letterbox_chain(F.FKL_E4M3, out=side, pad=cfg["pad"]))
+    dst = torch.empty((n, 3, side, side), dtype=torch.float8_e4m3fn, device="cuda")
+    o = F.as_fkl(dst, F.FKL_LAYOUT_NCHW)
+    stats = torch.zeros(32, dtype=torch.float32, device="cuda")
+    sp = stats.data_ptr()
+    with torch.cuda.stream(stream):
+        F.fkl_pipeline_autotune(p.handle, ins, None, o, stream=stream, reps=args.autotune_reps)
+
+        def red(st):
+            F.fkl_reduce_batch(p.handle, ins, None, o, sp, stream=st)
+
+        def step(st):
+            red(st)
+            F.fkl_execute_batch_scaled(p.handle, ins, None, o, sp + 11 * 4, stream=st)
+        for _ in range(3):
+            step(stream)
+        torch.cuda.synchronize()
+        k = args.secondary_steps
+        ms = float(np.mean(time_steps(torch, step, k, stream)))
+        red_ms = float(np.mean(time_steps(torch, red, k, stream)))
+    read_b, write_b = n * h * w * 3 // 2, n * 3 * side * side
+    return {"workload": f"NV12 {n}x{w}x{h} -> letterbox {side}x{side} -> x1/255 -> FP8-E4M3 with the scale "
+                        f"amax/448 from ReduceDPP (reduce pass, then the scaled write)",
+            "ms_per_step": round(ms, 5), "value": round((read_b + write_b) / (ms * 1e-3) / 1e9, 1), "unit": "GB/s",
+            "steps": k, "reduce_ms": round(red_ms, 5),
+            "reduce_GBps": round(read_b / (red_ms * 1e-3) / 1e9, 1),
+            "reduce_frac": round(read_b / (red_ms * 1e-3) / 1e9 / peak, 4),
+            "scale": round(float(stats[10].item()), 9)}
 
 
 def run_ours(args):
@@ -665,6 +716,65 @@ def cpu_baseline_parallel(wl, args):
                       f"float64 numpy (one thread per process)"}
 
 
+def serve_setup(F, W, synth, torch, n_pool, n_requests):
+    """The serving workload: a pool of pinned host images of 320-3840 x
+    240-2160 and requests of 1-64 of them (seeded)."""
+    rng = np.random.default_rng(4)
+    pool = []
+    for k in range(n_pool):
+        w, h = int(rng.integers(320, 3841)), int(rng.integers(240, 2161))
+        pool.append(torch.from_numpy(synth.packed_image(1000 + k, h, w)).pin_memory())
+    reqs = [list(rng.integers(0, len(pool), int(rng.integers(1, 65)))) for _ in range(n_requests)]
+    pipe = F.Pipeline(W.normalize_chain(224, 224, out_dtype=F.FKL_F16))
+    fk = [[F.as_fkl(pool[i]) for i in r] for r in reqs]
+    return pool, reqs, pipe, fk
+
+
+def serve_rate(F, synth, pipe, fk, rate, mode, slots, arena_gb, ctas_per_sm):
+    """Requests submitted at seeded Poisson arrival times against one server;
+    latency = completion minus scheduled arrival."""
+    arrivals = synth.poisson_arrivals(4, rate, len(fk))
+    srv = F.fkl_server_create(pipe.handle, mode, max_inflight=slots, arena_bytes=arena_gb << 30,
+                              ctas_per_sm=ctas_per_sm)
+    try:
+        # warm-up: one request through the server
+        rid = F.fkl_server_submit(srv, fk[0])
+        F.fkl_server_wait(srv, rid, 60000)
+        F.fkl_server_release(srv, rid)
+        t0 = time.monotonic() + 0.01
+        live, lat, q, h2d, nimg = {}, [], [], [], 0
+        i = 0
+        t_last = t0
+        while i < len(fk) or live:
+            now = time.monotonic()
+            while i < len(fk) and t0 + arrivals[i] <= now:
+                live[F.fkl_server_submit(srv, fk[i])] = t0 + arrivals[i]
+                i += 1
+            for rid in list(live):
+                done, _ = F.fkl_server_poll(srv, rid)
+                if done:
+                    info = F.fkl_server_request_info(srv, rid)
+                    lat.append(info.t_done - live.pop(rid))
+                    q.append(info.t_admit - info.t_submit)
+                    h2d.append(info.t_ready - info.t_admit)
+                    nimg += info.n_images
+                    t_last = max(t_last, info.t_done)
+                    F.fkl_server_release(srv, rid)
+            time.sleep(0.0001)
+        st = F.fkl_server_get_stats(srv)
+    finally:
+        F.fkl_server_destroy(srv)
+    lat_ms = np.array(lat) * 1e3
+    return {"rate_req_s": rate, "requests": len(fk), "images": nimg,
+            "p50_ms": round(float(np.percentile(lat_ms, 50)), 3),
+            "p99_ms": round(float(np.percentile(lat_ms, 99)), 3),
+            "queue_p50_ms": round(float(np.median(q)) * 1e3, 3),
+            "h2d_p50_ms": round(float(np.median(h2d)) * 1e3, 3),
+            "images_per_s": round(nimg / (t_last - t0), 1),
+            "kernel_launches": int(st.kernel_launches),
+            "arena_peak_gb": round(st.arena_peak_bytes / 2**30, 3)}
+
+
 def run_serve(args):
     """Serving loop: Poisson arrivals of requests of 1-64 images of mixed
     sizes (320-3840 x 240-2160) through fkl_server_*, full-frame resize to
@@ -675,57 +785,12 @@ def run_serve(args):
     __graft_entry__.build()
     from paper_2508_07071_gb300 import fkl as F, synth, workloads as W
 
-    rng = np.random.default_rng(4)
-    pool = []
-    for k in range(args.pool):
-        w, h = int(rng.integers(320, 3841)), int(rng.integers(240, 2161))
-        pool.append(torch.from_numpy(synth.packed_image(1000 + k, h, w)).pin_memory())
-    reqs = [list(rng.integers(0, len(pool), int(rng.integers(1, 65)))) for _ in range(args.requests)]
-    pipe = F.Pipeline(W.normalize_chain(224, 224, out_dtype=F.FKL_F16))
-    fk = [[F.as_fkl(pool[i]) for i in r] for r in reqs]
+    _, _, pipe, fk = serve_setup(F, W, synth, torch, args.pool, args.requests)
     results = []
     for rate in [float(x) for x in args.rates.split(",")]:
-        arrivals = synth.poisson_arrivals(4, rate, len(reqs))
         for mode, mname in ((F.FKL_SERVE_PERSISTENT, "persistent"), (F.FKL_SERVE_UNFUSED, "unfused_per_request")):
-            srv = F.fkl_server_create(pipe.handle, mode, max_inflight=args.slots, arena_bytes=args.arena_gb << 30,
-                                      ctas_per_sm=args.ctas_per_sm)
-            try:
-                # warm-up: one request through the server
-                rid = F.fkl_server_submit(srv, fk[0])
-                F.fkl_server_wait(srv, rid, 60000)
-                F.fkl_server_release(srv, rid)
-                t0 = time.monotonic() + 0.01
-                live, lat, q, h2d, nimg = {}, [], [], [], 0
-                i = 0
-                t_last = t0
-                while i < len(reqs) or live:
-                    now = time.monotonic()
-                    while i < len(reqs) and t0 + arrivals[i] <= now:
-                        live[F.fkl_server_submit(srv, fk[i])] = t0 + arrivals[i]
-                        i += 1
-                    for rid in list(live):
-                        done, _ = F.fkl_server_poll(srv, rid)
-                        if done:
-                            info = F.fkl_server_request_info(srv, rid)
-                            lat.append(info.t_done - live.pop(rid))
-                            q.append(info.t_admit - info.t_submit)
-                            h2d.append(info.t_ready - info.t_admit)
-                            nimg += info.n_images
-                            t_last = max(t_last, info.t_done)
-                            F.fkl_server_release(srv, rid)
-                    time.sleep(0.0001)
-                st = F.fkl_server_get_stats(srv)
-            finally:
-                F.fkl_server_destroy(srv)
-            lat_ms = np.array(lat) * 1e3
-            results.append({"rate_req_s": rate, "mode": mname, "requests": len(reqs), "images": nimg,
-                            "p50_ms": round(float(np.percentile(lat_ms, 50)), 3),
-                            "p99_ms": round(float(np.percentile(lat_ms, 99)), 3),
-                            "queue_p50_ms": round(float(np.median(q)) * 1e3, 3),
-                            "h2d_p50_ms": round(float(np.median(h2d)) * 1e3, 3),
-                            "images_per_s": round(nimg / (t_last - t0), 1),
-                            "kernel_launches": int(st.kernel_launches),
-                            "arena_peak_gb": round(st.arena_peak_bytes / 2**30, 3)})
+            r = serve_rate(F, synth, pipe, fk, rate, mode, args.slots, args.arena_gb, args.ctas_per_sm)
+            results.append({"rate_req_s": rate, "mode": mname, **{k: v for k, v in r.items() if k != "rate_req_s"}})
             print(json.dumps(results[-1]), flush=True)
     print(json.dumps({"metric": "serving latency and throughput", "workload": "Poisson requests, 1-64 u8 BGR "
                       "images 320-3840 x 240-2160 -> 224x224 RGB normalised planar f16", "results": results}),
@@ -1001,6 +1066,8 @@ def main():
                     help="nv12: also measure the other workloads (single image, crop batch, vertical chain "
                          "L=10/1000, FP8 and f16 outputs) into the line's `configs`")
     ap.add_argument("--secondary-steps", type=int, default=20)
+    ap.add_argument("--serve-requests", type=int, default=100,
+                    help="nv12 default run: requests of the serving measurement in `configs` (0: skip)")
     ap.add_argument("--e2e-steps", type=int, default=10)
     ap.add_argument("--cpu-seconds", type=float, default=10.0)
     ap.add_argument("--no-cpu-parallel", action="store_true",
