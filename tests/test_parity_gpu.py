@@ -1229,3 +1229,18 @@ def test_tile_staged_reader_falls_back_when_a_span_is_too_wide(F, W):
     want = O.preprocess_packed(src, (0, 0, 16384, 24), 128, 12, swap=True, mul=1 / 255,
                                sub=W.IMAGENET_MEAN, div=W.IMAGENET_STD)
     check_f32(to_numpy(base)[0], want, "16384 -> 128")
+
+
+@pytest.mark.parametrize("w", [724, 722])
+def test_per_op_nv12_decode_widths(F, W, w):
+    """The per-op decode kernel with coalesced stores (window width a multiple
+    of 4; 724 ends in a partial 128-pixel segment) and the generic decode
+    (722): both give the fused kernel's bytes."""
+    frames = synth.nv12_frames(38, 3, 362, w)
+    dev = [torch.from_numpy(f).cuda() for f in frames]
+    ops = [F.read_nv12(), F.letterbox(300, 200, 114.0), F.mul(W.INV255), F.write_split(F.FKL_BF16)]
+    fused = run_batch(F, ops, dev, None, (3, 3, 200, 300), "bf16", layout_in=F.FKL_LAYOUT_NV12)
+    got, _, _ = _per_op(F, ops, dev, None, (3, 3, 200, 300), "bf16", F.FKL_LAYOUT_NV12)
+    assert torch.equal(got.view(torch.int16), fused.view(torch.int16))
+    want = O.split(O.multiply(O.letterbox(O.nv12_to_rgb(frames[2]), 300, 200, 114.0), 1 / 255))
+    check_output(got[2], want, "bf16", 1.0, f"per-op width {w}")
