@@ -20,10 +20,8 @@ struct VChainParams {
   int32_t len;        // ops in this launch (<= CAP)
   int32_t alternating;  // 1: kinds are Mul, Add, Mul, Add, ... from op 0
   uint32_t add_mask[(CAP + 31) / 32];  // bit i set: op i is an Add
-  float c[CAP];                        // 8-byte aligned (32 + 4 * ceil(CAP / 32) bytes in)
+  alignas(16) float c[CAP];            // two Mul/Add pairs are read as one 16-byte vector
 };
-static_assert((32 + 4 * ((128 + 31) / 32)) % 8 == 0 && (32 + 4 * ((4096 + 31) / 32)) % 8 == 0,
-              "constant pairs are read as 8-byte vectors");
 
 // E consecutive input elements as floats (vector loads when `vec`).
 template <class InT, int E>
@@ -84,6 +82,19 @@ FKL_D void vchain_load(const void* in, int64_t base, int64_t n, bool vec, float 
   }
 }
 
+// One Mul, Add pair on the thread's E elements: fl(fl(x * cm) + ca).
+template <int E>
+FKL_D void vchain_pair(float (&x)[E], float cm, float ca) {
+  const F2 m = f2s(cm);
+#pragma unroll
+  for (int e = 0; e < E; e += 2) {
+    float lo, hi;
+    f2split(f2mul(f2(x[e], x[e + 1]), m), lo, hi);
+    x[e] = __fadd_rn(lo, ca);
+    x[e + 1] = __fadd_rn(hi, ca);
+  }
+}
+
 template <int E, int CAP, bool kAlt, class InT = float>
 __global__ void __launch_bounds__(512) vchain_kernel(const __grid_constant__ VChainParams<CAP> p) {
   static_assert(E == 2 || E % 4 == 0, "2 or a multiple of 4 elements per thread");
@@ -96,27 +107,26 @@ __global__ void __launch_bounds__(512) vchain_kernel(const __grid_constant__ VCh
                       (reinterpret_cast<uintptr_t>(p.out) & 15) == 0;
     vchain_load<InT, E>(p.in, base, p.n, full, x);
     if constexpr (kAlt) {
-      // Mul, Add pairs: no per-op branch; each pair's two constants come in
-      // one 8-byte load, and four pairs per loop trip amortise the loop.
-      // The Mul runs on two elements per packed f32x2 multiply and the Add
-      // on scalar adds: three FP32 issue slots per two elements and pair
-      // instead of four, for the same FP32 lane work, so the constant loads
-      // and the loop fit beside the FP32 pipe. (A packed multiply feeding a
-      // packed add is contracted into a multiply-add by the assembler, which
-      // rounds once where the chain rounds twice; with either side scalar it
-      // is not.)
+      // Mul, Add pairs: no per-op branch; two pairs' four constants come in
+      // one 16-byte load (one load per pair ran 8% slower on small batches,
+      // where few warps per scheduler leave the loads exposed), and eight
+      // pairs per loop trip amortise the loop. The Mul runs on two elements
+      // per packed f32x2 multiply and the Add on scalar adds: three FP32
+      // issue slots per two elements and pair instead of four, for the same
+      // FP32 lane work, so the constant loads and the loop fit beside the
+      // FP32 pipe. (A packed multiply feeding a packed add is contracted into
+      // a multiply-add by the assembler, which rounds once where the chain
+      // rounds twice; with either side scalar it is not.)
       int i = 0;
 #pragma unroll 4
+      for (; i + 3 < p.len; i += 4) {
+        const float4 cc = *reinterpret_cast<const float4*>(&p.c[i]);  // i % 4 == 0: 16-byte aligned
+        vchain_pair<E>(x, cc.x, cc.y);
+        vchain_pair<E>(x, cc.z, cc.w);
+      }
       for (; i + 1 < p.len; i += 2) {
         const float2 cc = *reinterpret_cast<const float2*>(&p.c[i]);  // i is even: 8-byte aligned
-        const F2 cm = f2s(cc.x);
-#pragma unroll
-        for (int e = 0; e < E; e += 2) {
-          float lo, hi;
-          f2split(f2mul(f2(x[e], x[e + 1]), cm), lo, hi);
-          x[e] = __fadd_rn(lo, cc.y);
-          x[e + 1] = __fadd_rn(hi, cc.y);
-        }
+        vchain_pair<E>(x, cc.x, cc.y);
       }
       if (i < p.len) {
         const float cm = p.c[i];
