@@ -356,15 +356,17 @@ FKL_API fkl_status fkl_execute_batch_unfused_static(fkl_pipeline p, int32_t n, c
  * How: the ROp is evaluated once per pixel of each image's placed window and
  * its per-channel extremes and sum are reduced; the COps of these chains
  * (SWAP_RB, MUL, ADD/SUB, DIV by per-channel constants, each rounded) are
- * monotone and affine on every channel, so the finishing kernel maps the
- * read values' extremes through them (the result equals the extremes of
- * the values fkl_execute_batch writes with an F32 output, bit for bit) and
- * the mean through the affine map in float64; fill pixels (the letterbox
- * pad) join on the host's count. Min/max are exact; sums are accumulated in
- * 64-bit fixed point (2^-20 read units), independent of the grid and of the
- * order in which blocks finish. Launches: two memsets, one reduction launch
- * per 256 images and one finishing kernel. An empty batch (n = 0) leaves NaN
- * extremes, mean 0, amax 0 and s = 1.
+ * monotone and affine on every channel, so the block that finishes last
+ * maps the read values' extremes through them (the result equals the
+ * extremes of the values fkl_execute_batch writes with an F32 output, bit
+ * for bit) and the mean through the affine map in float64; fill pixels (the
+ * letterbox pad) join on the host's count. Min/max are exact; sums are
+ * accumulated in 64-bit fixed point (2^-10 read units), independent of the
+ * grid and of the order in which blocks finish. Launches: one memset of the
+ * accumulator and one reduction launch per 256 images (a call without any
+ * window pixel launches one small kernel that writes the statistics
+ * instead). Calls that share a `stats` buffer must not overlap on the GPU.
+ * An empty batch (n = 0) leaves NaN extremes, mean 0, amax 0 and s = 1.
  */
 #define FKL_REDUCE_STATS_BYTES 128
 FKL_API fkl_status fkl_reduce_batch(fkl_pipeline p, int32_t n, const fkl_tensor* ins, const int32_t* rois,

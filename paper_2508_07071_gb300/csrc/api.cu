@@ -843,10 +843,14 @@ fkl_status fkl_reduce_batch(fkl_pipeline p, int32_t n, const fkl_tensor* ins, co
   auto* acc = reinterpret_cast<fkl::ReduceAcc*>(reinterpret_cast<uint8_t*>(stats) + 64);
   static_assert(sizeof(fkl::ReduceAcc) <= 64, "accumulator fits the stats buffer");
   cudaError_t e = cudaMemsetAsync(acc, 0, sizeof(fkl::ReduceAcc), s);
-  if (e == cudaSuccess) e = cudaMemsetAsync(acc->min_key, 0xFF, sizeof(acc->min_key), s);
-  ReduceLaunch info;
   double fill = 0.0;  // output pixels outside the placed windows: the pad value
   for (const auto& r : imgs) fill += static_cast<double>(od.H) * od.W - static_cast<double>(r.dw) * r.dh;
+  // every chunk's launch is sized first: the block that completes the
+  // blocks of all of them writes the statistics
+  std::vector<LaunchCtx> chunks;
+  std::vector<ReducePlan> plans;
+  int64_t jobs = 0, blocks = 0;
+  int grid = 0;
   for (int start = 0; start < n && e == cudaSuccess; start += kBatchCap) {
     LaunchCtx c;
     c.spec = &p->spec;
@@ -859,10 +863,20 @@ fkl_status fkl_reduce_batch(fkl_pipeline p, int32_t n, const fkl_tensor* ins, co
     c.stream = s;
     c.all_exact2x = true;
     for (int i = 0; i < c.n; ++i) c.all_exact2x = c.all_exact2x && (c.imgs[i].flags & fkl::kExact2x);
-    e = launch_reduce(c, acc, info);
+    ReducePlan pl;
+    e = plan_reduce(c, pl);
+    jobs += pl.jobs;
+    blocks += pl.grid;
+    grid = std::max(grid, pl.grid);
+    chunks.push_back(c);
+    plans.push_back(pl);
   }
-  if (e == cudaSuccess)
-    e = finalize_reduce(p->spec, acc, static_cast<double>(n) * od.H * od.W, fill, info, stats, s);
+  if (e == cudaSuccess) {
+    const fkl::ReduceFinal fin =
+        reduce_final(p->spec, stats, static_cast<double>(n) * od.H * od.W, fill, jobs, grid, blocks);
+    if (blocks == 0) e = finish_reduce(acc, fin, s);
+    for (size_t i = 0; i < chunks.size() && e == cudaSuccess; ++i) e = launch_reduce(chunks[i], plans[i], acc, fin);
+  }
   return e == cudaSuccess ? FKL_OK : cuda_fail(e, "reduction");
 }
 

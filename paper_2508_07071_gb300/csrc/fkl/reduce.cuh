@@ -30,11 +30,16 @@ namespace fkl {
 // pixel by pixel. Every job's partial sums become 64-bit fixed point (2^-10
 // read units), min/max travel as order-preserving unsigned keys, so the
 // result does not depend on the grid or on the order in which blocks finish.
+// The last block of a call to finish (a counter over every launch of the
+// call) maps the accumulator into the statistics, so a call is one memset
+// of the accumulator and one launch per 256 images.
 // ---------------------------------------------------------------------------
 struct ReduceAcc {
-  unsigned int min_key[3];       // extremes of the ROp's values per channel
-  unsigned int max_key[3];
+  unsigned int min_inv[3];       // per channel, ~(order key) of the ROp's minimum: the maximum
+                                 // of the inverted keys, so that zero is the identity
+  unsigned int max_key[3];       // order key of the maximum
   unsigned long long sum_fx[3];  // fixed point, 2^-10 read units
+  unsigned int done;             // blocks finished, over every launch of one call
 };
 // Sums: every job's float32 partial sum (of at most 16 values below 256,
 // or 16 tap sums below 4) is scaled to 2^-10 read units -- below 2^22 --
@@ -67,12 +72,75 @@ FKL_D float max3f(float a, float b, float c) {
   return d;
 }
 
+// The chain's statistics from the ROp's (paper §IV-C: the COps applied to
+// the reduced values). Per output channel c the read channel is c, or 2 - c
+// after a BGR <-> RGB swap; the fill (letterbox) value joins the extremes
+// and the sum when the output has fill pixels.
+struct ReduceChain {
+  int32_t swap;
+  int32_t has_div;
+  float mul[3], sub[3], div[3];
+  float pad;
+};
+
+FKL_D float apply_reduce_chain(const ReduceChain& ch, int c, float x) {
+  x = __fmul_rn(x, ch.mul[c]);
+  x = __fsub_rn(x, ch.sub[c]);
+  return ch.has_div ? __fdiv_rn(x, ch.div[c]) : x;
+}
+
+// What the block that completes a call needs to write the statistics.
+struct ReduceFinal {
+  float* stats;
+  double count;       // output pixels per channel
+  double fill_count;  // of them, fill pixels (the pad value)
+  ReduceChain chain;
+  int32_t jobs, grid;  // the work split reported in the statistics
+  uint32_t blocks;     // blocks of all the call's reduction launches
+};
+
+// The statistics of include/fkl.h from the accumulator (one thread). Reads
+// go through volatile loads: the other blocks' atomics are in L2.
+FKL_D void reduce_finish(const ReduceAcc* acc_in, const ReduceFinal& f) {
+  const volatile ReduceAcc* acc = acc_in;
+  float* stats = f.stats;
+  const ReduceChain& ch = f.chain;
+  float amax = 0.f;
+  for (int c = 0; c < 3; ++c) {
+    const int rc = ch.swap ? 2 - c : c;  // the read channel output channel c comes from
+    float lo = key_value(~acc->min_inv[rc]);
+    float hi = key_value(acc->max_key[rc]);
+    if (f.fill_count > 0) {
+      lo = fminf(lo, ch.pad);
+      hi = fmaxf(hi, ch.pad);
+    }
+    const float a = apply_reduce_chain(ch, c, lo), b = apply_reduce_chain(ch, c, hi);
+    stats[c] = f.count > 0 ? fminf(a, b) : __int_as_float(0x7fc00000);
+    stats[3 + c] = f.count > 0 ? fmaxf(a, b) : __int_as_float(0x7fc00000);
+    // the mean: the chain's affine map of the read values' mean, in float64
+    const double sum = static_cast<double>(static_cast<long long>(acc->sum_fx[rc])) / kSumScale +
+                       f.fill_count * static_cast<double>(ch.pad);
+    double m = f.count > 0 ? sum / f.count : 0.0;
+    m = (m * ch.mul[c] - ch.sub[c]) / (ch.has_div ? static_cast<double>(ch.div[c]) : 1.0);
+    stats[6 + c] = f.count > 0 ? static_cast<float>(m) : 0.f;
+    // the largest magnitude is that of a channel's minimum or maximum
+    if (f.count > 0) amax = fmaxf(amax, fmaxf(fabsf(stats[c]), fabsf(stats[3 + c])));
+  }
+  stats[9] = amax;
+  const float s = amax > 0.f ? __fdiv_rn(amax, 448.f) : 1.f;  // E4M3 per-tensor scale
+  stats[10] = s;
+  stats[11] = __fdiv_rn(1.f, s);
+  reinterpret_cast<int32_t*>(stats)[12] = f.jobs;
+  reinterpret_cast<int32_t*>(stats)[13] = f.grid;
+}
+
 template <class RB>
 struct ReduceArgs {
   typename RB::ParamsType rp;
   int32_t col_tiles;  // jobs per window row band: ceil(ceil(max dw / V) / blockDim.x)
   int32_t row_tiles;  // row bands per image: ceil(max dh / blockDim.y)
   ReduceAcc* acc;
+  ReduceFinal fin;
 };
 
 // A thread's running statistics on the exact-2x span: extremes of the tap
@@ -274,9 +342,16 @@ FKL_D void reduce2d_body(const ReduceArgs<RB>& a) {
   }
   __syncthreads();
   if (tid < 3) {
-    atomicMin(&a.acc->min_key[tid], sh.min_key[tid]);
+    atomicMax(&a.acc->min_inv[tid], ~sh.min_key[tid]);
     atomicMax(&a.acc->max_key[tid], sh.max_key[tid]);
     atomicAdd(&a.acc->sum_fx[tid], sh.sum_fx[tid]);
+    __threadfence();  // this block's totals before its count below
+  }
+  __syncthreads();
+  // the block that completes the call's count writes the statistics
+  if (tid == 0 && atomicAdd(&a.acc->done, 1u) + 1u == a.fin.blocks) {
+    __threadfence();
+    reduce_finish(a.acc, a.fin);
   }
 }
 
@@ -286,23 +361,6 @@ template <int V, int kMinBlocks, class RB>
 __global__ void __launch_bounds__(256, kMinBlocks > 0 ? kMinBlocks : 1)
     reduce2d_kernel(const __grid_constant__ ReduceArgs<RB> a) {
   reduce2d_body<V>(a);
-}
-
-// The chain's statistics from the ROp's (paper §IV-C: the COps applied to
-// the reduced values). Per output channel c the read channel is c, or 2 - c
-// after a BGR <-> RGB swap; the fill (letterbox) value joins the extremes
-// and the sum when the output has fill pixels.
-struct ReduceChain {
-  int32_t swap;
-  int32_t has_div;
-  float mul[3], sub[3], div[3];
-  float pad;
-};
-
-FKL_D float apply_reduce_chain(const ReduceChain& ch, int c, float x) {
-  x = __fmul_rn(x, ch.mul[c]);
-  x = __fsub_rn(x, ch.sub[c]);
-  return ch.has_div ? __fdiv_rn(x, ch.div[c]) : x;
 }
 
 }  // namespace fkl

@@ -10,7 +10,8 @@
 #include "fkl/dpp.cuh"
 
 namespace fkl {
-struct ReduceAcc;  // fkl/reduce.cuh
+struct ReduceAcc;    // fkl/reduce.cuh
+struct ReduceFinal;  // fkl/reduce.cuh
 }  // namespace fkl
 
 namespace fkl_impl {
@@ -76,18 +77,24 @@ cudaError_t launch_nv12_bf16(const LaunchCtx& c);
 cudaError_t launch_nv12_e4m3(const LaunchCtx& c);
 // Integer chains (k_int.cu).
 cudaError_t launch_int(const LaunchCtx& c);
-// ReduceDPP over a float image chain (k_reduce.cu): launch_reduce reduces
-// the ROp's values over each image's placed window into `acc` (initialised
-// by the caller) and adds its work split to `info`; finalize_reduce maps the
-// accumulator through the chain's COps into the statistics of include/fkl.h
-// (`count` output pixels per channel, `fill_count` of them fill pixels).
-struct ReduceLaunch {
-  int64_t jobs = 0;  // jobs of all reduction launches
-  int grid = 0;      // blocks of the largest launch
+// ReduceDPP over a float image chain (k_reduce.cu). plan_reduce sizes the
+// reduction launch of one chunk of at most kBatchCap images (grid 0: no
+// window pixels, no launch); launch_reduce reduces the ROp's values over
+// each image's placed window into `acc` (zeroed by the caller), and the
+// block that completes `fin.blocks`, the blocks of all the call's launches,
+// writes the statistics of include/fkl.h; finish_reduce writes them for a
+// call that launched nothing. reduce_final describes the call: `count`
+// output pixels per channel, `fill_count` of them fill pixels.
+struct ReducePlan {
+  int32_t col_tiles = 0, row_tiles = 0;
+  int64_t jobs = 0;
+  int grid = 0;
 };
-cudaError_t launch_reduce(const LaunchCtx& c, fkl::ReduceAcc* acc, ReduceLaunch& info);
-cudaError_t finalize_reduce(const Spec& s, const fkl::ReduceAcc* acc, double count, double fill_count,
-                            const ReduceLaunch& info, float* stats, cudaStream_t st);
+cudaError_t plan_reduce(const LaunchCtx& c, ReducePlan& pl);
+cudaError_t launch_reduce(const LaunchCtx& c, const ReducePlan& pl, fkl::ReduceAcc* acc, const fkl::ReduceFinal& fin);
+fkl::ReduceFinal reduce_final(const Spec& s, float* stats, double count, double fill_count, int64_t jobs, int grid,
+                              int64_t blocks);
+cudaError_t finish_reduce(const fkl::ReduceAcc* acc, const fkl::ReduceFinal& fin, cudaStream_t st);
 // Vertical chain (k_vchain.cu): one fused launch per chunk of ops.
 constexpr int kVChainCap = 4096;
 cudaError_t launch_vchain(const Spec& s, const fkl_launch_shape& shape, const void* in, float* out,

@@ -1244,3 +1244,42 @@ def test_per_op_nv12_decode_widths(F, W, w):
     assert torch.equal(got.view(torch.int16), fused.view(torch.int16))
     want = O.split(O.multiply(O.letterbox(O.nv12_to_rgb(frames[2]), 300, 200, 114.0), 1 / 255))
     check_output(got[2], want, "bf16", 1.0, f"per-op width {w}")
+
+
+def test_reduce_over_two_launches_twice_on_one_buffer(F, W):
+    """300 images take two reduction launches (256 images each at most); the
+    block that completes both writes the statistics. The same stats buffer
+    is used twice in a row: the second call starts from a cleared
+    accumulator and gives the same bytes. Extremes equal the float32
+    write's; mean and amax match the oracle."""
+    n = 300
+    src = synth.packed_image(31, 48, 64)
+    rng = np.random.default_rng(5)
+    rois = np.zeros((n, 4), np.int32)
+    for i in range(n):
+        w, h = int(rng.integers(8, 65)), int(rng.integers(6, 49))
+        rois[i] = (int(rng.integers(0, 64 - w + 1)), int(rng.integers(0, 48 - h + 1)), w, h)
+    ops = [F.read_u8c3(), F.resize(40, 30), F.swap_rb(), F.mul(1 / 255), F.sub(W.IMAGENET_MEAN),
+           F.div(W.IMAGENET_STD), F.write_split(F.FKL_F32)]
+    d = torch.from_numpy(src).cuda()
+    got = run_batch(F, ops, [d] * n, rois, (n, 3, 30, 40), "f32")
+    p = F.Pipeline(ops)
+    runs = []
+    for _ in range(2):
+        stats = torch.full((32,), 7.0, device="cuda") if not runs else runs[0][1]
+        F.fkl_reduce_batch(p.handle, [F.as_fkl(d)] * n, rois, F.as_fkl(got, F.FKL_LAYOUT_NCHW), stats.data_ptr())
+        torch.cuda.synchronize()
+        runs.append((stats[:14].clone(), stats))
+    assert torch.equal(runs[0][0].view(torch.int32), runs[1][0].view(torch.int32))
+    st, jobs, grid = _reduce_split(runs[1][1])
+    assert jobs > grid > 0
+    per_c = got.permute(1, 0, 2, 3).reshape(3, -1)
+    assert np.array_equal(st[0:3].astype(np.float32), per_c.min(dim=1).values.cpu().numpy())
+    assert np.array_equal(st[3:6].astype(np.float32), per_c.max(dim=1).values.cpu().numpy())
+    vals = O.preprocess_packed_batch([src] * n, rois, 40, 30, swap=True, mul=1 / 255,
+                                     sub=W.IMAGENET_MEAN, div=W.IMAGENET_STD)
+    want = O.reduce_stats(vals)
+    check_f32(st[0:3], want["min"], "min")
+    check_f32(st[3:6], want["max"], "max")
+    np.testing.assert_allclose(st[6:9], want["mean"], rtol=1e-5, atol=1e-6)
+    check_f32(st[9], want["amax"], "amax")
