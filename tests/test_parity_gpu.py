@@ -241,8 +241,12 @@ def test_nv12_resize_with_normalise(F, W):
 # ------------------------------------------------------------------ vertical chain
 
 
-@pytest.mark.parametrize("L", [0, 1, 2, 10, 100, 1000, 4099])
+@pytest.mark.parametrize("L", [0, 1, 2, 7, 10, 13, 100, 1000, 4099])
 def test_vertical_chain_bit_exact(F, W, L):
+    """Alternating Mul/Add chains against the same-order float32 oracle, bit
+    for bit. The kernel reads the constants of two pairs at a time, then of
+    one pair, then a lone Mul: lengths 7 and 13 take all three steps in one
+    launch, 4099 two launches."""
     n = 100_003
     x = synth.f32_uniform(2, n)
     kinds, consts = synth.chain_constants(2, L)
