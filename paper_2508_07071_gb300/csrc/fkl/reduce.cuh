@@ -17,7 +17,7 @@ namespace fkl {
 // and f is affine, so the mean of f is f of the mean, up to the rounding of
 // the per-pixel values. The kernel therefore reduces the ROp's values only,
 // over the placed window of every image (the fill around it is one known
-// value, counted on the host), and the finishing kernel maps the statistics
+// value, counted on the host), and the finishing block maps the statistics
 // through the COps once. The extremes are the same floats the TransformDPP
 // writes.
 //

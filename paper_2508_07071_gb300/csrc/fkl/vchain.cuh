@@ -108,9 +108,9 @@ __global__ void __launch_bounds__(512) vchain_kernel(const __grid_constant__ VCh
     vchain_load<InT, E>(p.in, base, p.n, full, x);
     if constexpr (kAlt) {
       // Mul, Add pairs: no per-op branch; two pairs' four constants come in
-      // one 16-byte load (one load per pair ran 8% slower on small batches,
-      // where few warps per scheduler leave the loads exposed), and eight
-      // pairs per loop trip amortise the loop. The Mul runs on two elements
+      // one 16-byte load (one 8-byte load per pair ran 8% slower on a
+      // 360,000-element batch), and eight pairs per loop trip amortise the
+      // loop. The Mul runs on two elements
       // per packed f32x2 multiply and the Add on scalar adds: three FP32
       // issue slots per two elements and pair instead of four, for the same
       // FP32 lane work, so the constant loads and the loop fit beside the
