@@ -562,7 +562,11 @@ FKL_API const char* fkl_pipeline_kernel_name(fkl_pipeline p);
  * even y offset, pitch a multiple of 16, 16-byte aligned base) that fills the
  * output width, and the output width is a multiple of `vec`; any other launch
  * of the pipeline runs the register kernel with a 32 x 8 block and RY = 1.
- * Both give the same bytes. */
+ * Packed-image chains, RY = -1 (V <= 4): the tile-staged reader; each block
+ * stages the source bytes its tile's taps reference in shared memory before
+ * blending (when every image's span fits 48 KB, else the register kernel
+ * with a 32 x 8 block and RY = 1).
+ * All forms give the same bytes. */
 typedef struct {
   int32_t vec;      /* pixels (elements) per thread along x               */
   int32_t tx, ty;   /* threads per block along x and y                    */
