@@ -109,8 +109,8 @@ __global__ void __launch_bounds__(512) vchain_kernel(const __grid_constant__ VCh
     if constexpr (kAlt) {
       // Mul, Add pairs: no per-op branch; two pairs' four constants come in
       // one 16-byte load (one 8-byte load per pair ran 8% slower on a
-      // 360,000-element batch), and eight pairs per loop trip amortise the
-      // loop. The Mul runs on two elements
+      // 360,000-element batch), and sixteen pairs per loop trip amortise
+      // the loop (eight: 2% slower). The Mul runs on two elements
       // per packed f32x2 multiply and the Add on scalar adds: three FP32
       // issue slots per two elements and pair instead of four, for the same
       // FP32 lane work, so the constant loads and the loop fit beside the
@@ -118,7 +118,7 @@ __global__ void __launch_bounds__(512) vchain_kernel(const __grid_constant__ VCh
       // a multiply-add by the assembler, which rounds once where the chain
       // rounds twice; with either side scalar it is not.)
       int i = 0;
-#pragma unroll 4
+#pragma unroll 8
       for (; i + 3 < p.len; i += 4) {
         const float4 cc = *reinterpret_cast<const float4*>(&p.c[i]);  // i % 4 == 0: 16-byte aligned
         vchain_pair<E>(x, cc.x, cc.y);
