@@ -561,6 +561,14 @@ def run_ours(args):
         if between is not None:  # L2-sized workloads: also without the flush (inputs stay in L2)
             warm_ms = float(np.mean(time_steps_queued(torch, wl.step, min(args.steps, 100), stream)))
 
+        # the same step captured once in a CUDA graph and replayed
+        graph = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(graph, stream=stream):
+            wl.step(stream)
+        graph.replay()
+        torch.cuda.synchronize()
+        graph_ms = float(np.mean(time_steps(torch, lambda st: graph.replay(), min(args.steps, 100), stream, between)))
+
         # unfused chain on the same GPU (a few steps)
         ku = min(args.steps, args.unfused_steps)
         unfused = measure_unfused(torch, wl, ku, stream, between, ms_per_step, peak) if ku > 0 else None
@@ -612,6 +620,7 @@ def run_ours(args):
         "data": "synthetic (seeded), resident in HBM",
         "config": {"workload": wl.name, "algorithmic_bytes_per_step": int(wl.bytes),
                    "best_ms": round(float(np.min(times)), 5), "median_ms": round(float(np.median(times)), 5),
+                   "cuda_graph_ms_per_step": round(graph_ms, 5),
                    "sector_bytes_per_step": int(getattr(wl, "sector_bytes", wl.bytes)),
                    "warm_ms_per_step": None if warm_ms is None else round(warm_ms, 5),
                    "warm_value": None if warm_ms is None else round(wl.bytes / (warm_ms * 1e-3) / 1e9, 1),
